@@ -1,0 +1,150 @@
+/*
+ * polydet.h - C ABI of libpolydet: exact determinants of n x n matrices over
+ * Z[x1..xk] by the modular method of arXiv 2010.12117 (Wei & Chen,
+ * "Optimized Multivariate Polynomial Determinant on GPU"), on one GB300.
+ *
+ * Algorithm 1 of the paper runs, for every prime p_i, an evaluation on a grid
+ * of roots of unity (Sec. 3.1, Algorithm 2), a determinant of every evaluated
+ * matrix mod p_i (Sec. 3.2, Algorithm 3) and an interpolation (Sec. 3.3), then
+ * reconstructs the integer coefficients by mixed-radix CRT (Sec. 3.4,
+ * Algorithm 4).  Each stage is one call below; each call only enqueues work.
+ *
+ * Conventions for every call:
+ *  - Pointers marked "device" are CUDA device pointers owned by the caller
+ *    (the plan never frees them); pointers marked "host" are host memory.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls return after enqueueing kernels on it.
+ *  - Residues are plain (not Montgomery) integers in [0, p).
+ *  - Multi-index arrays are row-major with the last index fastest.
+ *  - Per-prime arrays passed with a range [prime_lo, prime_hi) start at prime
+ *    prime_lo: slot 0 of the array belongs to prime prime_lo.
+ *  - A negative return value is an error code; nothing was enqueued.  Device
+ *    side failures (a degree bound that did not hold, a bounded wait that ran
+ *    out) are recorded in the plan's status word, read by polydet_sync_status.
+ *
+ * Grid and coefficient layouts (Sec. 2, dense encoding, x1 slowest):
+ *  - entry coefficients: int32 [n][n][E], E = prod_v (d_v + 1), exponent
+ *    vectors (e1..ek) with 0 <= e_v <= d_v in lex order;
+ *  - evaluation grid: G = prod_v N_v nodes, N_v = nextpow2(D_v + 1),
+ *    D_v = n * d_v; node (i1..ik) is x_v = w_v^(i_v) with w_v = g^((p-1)/N_v)
+ *    for the least generator g of (Z/pZ)^*, flat index lex (i1 slowest);
+ *  - determinant coefficients: C = prod_v (D_v + 1), lex over e_v <= D_v.
+ */
+#ifndef POLYDET_H
+#define POLYDET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define POLYDET_OK 0
+#define POLYDET_EINVAL (-1)   /* bad argument (null, size, range, layout)   */
+#define POLYDET_EDEGREE (-2)  /* some N_v above POLYDET_MAX_GRID_DIM         */
+#define POLYDET_EPRIMES (-3)  /* more primes than the table holds            */
+#define POLYDET_ENOMEM (-4)   /* device allocation failed (plan only)        */
+#define POLYDET_ECUDA (-5)    /* a CUDA runtime call failed                  */
+#define POLYDET_ETIMEOUT (-6) /* a bounded device wait gave up               */
+#define POLYDET_EBOUND (-7)   /* interpolation found a coefficient beyond D_v */
+
+/* Bits of the device status word (polydet_sync_status). */
+#define POLYDET_STATUS_BOUND 0x1u   /* interpolation tail was nonzero */
+#define POLYDET_STATUS_TIMEOUT 0x2u /* a bounded wait gave up         */
+
+/* Limits. */
+#define POLYDET_MAX_N 32          /* matrix order                          */
+#define POLYDET_MAX_VARS 6        /* number of variables k                 */
+#define POLYDET_MAX_GRID_DIM 8192 /* N_v cap (the paper's MAX_FFT_DIM)     */
+#define POLYDET_MAX_PRIMES 91     /* primes c*2^20+1 in (2^30, 2^31)       */
+
+typedef struct polydet_plan_s *polydet_plan_t;
+
+typedef struct polydet_plan_info {
+  int32_t n;                       /* matrix order                         */
+  int32_t nvars;                   /* k                                    */
+  int32_t P;                       /* primes in the plan                   */
+  int32_t W;                       /* 32-bit words per output coefficient  */
+  int64_t E;                       /* coefficients per entry               */
+  int64_t G;                       /* grid nodes per prime                 */
+  int64_t C;                       /* determinant coefficients             */
+  int32_t d[POLYDET_MAX_VARS];     /* entry degree bound per variable      */
+  int32_t D[POLYDET_MAX_VARS];     /* determinant degree bound, n * d_v    */
+  int32_t N[POLYDET_MAX_VARS];     /* grid size per variable               */
+  uint64_t workspace_bytes;        /* device scratch owned by the plan     */
+} polydet_plan_info;
+
+/* Primes of Eq. 1 with q = 20: every p = c * 2^20 + 1 in (2^30, 2^31), largest
+ * first.  Returns the table size (91) when `out` is NULL, else writes that
+ * many values to host `out`. */
+int polydet_prime_table(uint32_t *out);
+
+/* Coefficient bound and prime count (Sec. 2: the product of the primes must
+ * exceed the bound; signed output needs more than twice the bound).
+ * bound = min over rows / columns of prod_i (sum_j l1[i][j]^2)^(1/2), where
+ * host `entry_l1` [n][n] holds the l1 norm of each entry's coefficients.
+ * Writes the smallest P >= 2 (Sec. 4.1 uses at least two primes) with
+ * sum_i log2 p_i > 1 + log2(bound) + 1e-6, and log2(bound).  Returns
+ * POLYDET_EPRIMES when the table is too short. */
+int polydet_hadamard_primes(int n, const int64_t *entry_l1, int *nprimes_out,
+                            double *log2_bound_out);
+
+/* Build a plan for n x n matrices in `nvars` variables whose entries have
+ * degree <= entry_deg[v] (host array) in x_v, using the first `nprimes`
+ * primes of the table (must be >= 1).  Allocates the plan's device tables
+ * (Montgomery constants, twiddles, Garner tables) and its workspace; later
+ * calls allocate nothing.  `flags` must be 0.  The plan must be destroyed
+ * with polydet_plan_destroy. */
+int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
+                 int nprimes, uint32_t flags);
+int polydet_plan_destroy(polydet_plan_t plan);
+int polydet_plan_query(polydet_plan_t plan, polydet_plan_info *info);
+/* Host copies: primes [P]; roots w_{q,v} as [P][nvars]. */
+int polydet_plan_primes(polydet_plan_t plan, uint32_t *primes_out);
+int polydet_plan_roots(polydet_plan_t plan, uint32_t *roots_out);
+
+/* Stage 1, evaluation (Sec. 3.1, Algorithm 2): for every prime q in
+ * [prime_lo, prime_hi) and entry e, the multivariate NTT of the zero-padded
+ * coefficients, i.e. the entry at every grid node mod p_q.
+ * coeffs_dev: device int32 [n*n][E] (|c| < 2^31).  evals_dev: device uint32
+ * [prime_hi - prime_lo][n*n][G]. */
+int polydet_eval(polydet_plan_t plan, const int32_t *coeffs_dev, int prime_lo,
+                 int prime_hi, uint32_t *evals_dev, void *stream);
+
+/* Stage 2, condensation (Sec. 3.2, Algorithm 3): det of the n x n matrix at
+ * every grid node mod p_q, by fraction-free elimination with a search for the
+ * first nonzero pivot.  evals_dev as written by polydet_eval; detvals_dev:
+ * device uint32 [prime_hi - prime_lo][G]. */
+int polydet_condense_batch(polydet_plan_t plan, const uint32_t *evals_dev,
+                           int prime_lo, int prime_hi, uint32_t *detvals_dev,
+                           void *stream);
+
+/* Stage 3, interpolation (Sec. 3.3): inverse NTT with the 1/N factor,
+ * keeping the C coefficients with e_v <= D_v.  Any nonzero coefficient with
+ * e_v > D_v sets POLYDET_STATUS_BOUND.  detvals_dev: device uint32
+ * [prime_hi - prime_lo][G] (read only); residues_dev: device uint32
+ * [prime_hi - prime_lo][C].  These per-prime residues are the restart point
+ * of a run (Sec. 4.3): a resumed run recomputes only the missing primes. */
+int polydet_interp(polydet_plan_t plan, const uint32_t *detvals_dev, int prime_lo,
+                   int prime_hi, uint32_t *residues_dev, void *stream);
+
+/* Stage 4, CRT (Sec. 3.4, Algorithm 4): mixed-radix (Garner) digits of each
+ * coefficient over all P primes, converted to the signed integer in
+ * (-M/2, M/2), M = prod p.  residues_dev: device uint32 [P][C]; limbs_dev:
+ * device uint32 [C][W], little-endian two's complement. */
+int polydet_crt(polydet_plan_t plan, const uint32_t *residues_dev, uint32_t *limbs_dev,
+                void *stream);
+
+/* Synchronise `stream`, return the plan's status word in *status_out and clear
+ * it.  Returns POLYDET_EBOUND / POLYDET_ETIMEOUT if the matching bit was set. */
+int polydet_sync_status(polydet_plan_t plan, void *stream, uint32_t *status_out);
+
+/* Last CUDA error string seen by the library (host, static storage). */
+const char *polydet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLYDET_H */

@@ -1,0 +1,213 @@
+"""Thin ctypes binding of libpolydet (``include/polydet.h``).
+
+Argument marshalling only: every stage of the determinant runs in the
+library's CUDA kernels.  Device buffers are torch CUDA tensors (int32
+storage; residues are reinterpreted as uint32), streams are torch streams.
+If the library has not been built this module raises on first use; there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libpolydet.so")
+
+MAX_VARS = 6
+OK, EINVAL, EDEGREE, EPRIMES, ENOMEM, ECUDA, ETIMEOUT, EBOUND = 0, -1, -2, -3, -4, -5, -6, -7
+_ERRNAMES = {EINVAL: "EINVAL", EDEGREE: "EDEGREE", EPRIMES: "EPRIMES", ENOMEM: "ENOMEM",
+             ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", EBOUND: "EBOUND"}
+
+
+class PolydetError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what} failed: {_ERRNAMES.get(code, code)} {last_error()}")
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nvars", ctypes.c_int32), ("P", ctypes.c_int32),
+                ("W", ctypes.c_int32), ("E", ctypes.c_int64), ("G", ctypes.c_int64),
+                ("C", ctypes.c_int64), ("d", ctypes.c_int32 * MAX_VARS),
+                ("D", ctypes.c_int32 * MAX_VARS), ("N", ctypes.c_int32 * MAX_VARS),
+                ("workspace_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); the exported C ABI.
+_VP, _I, _U32, _PI32, _PU32, _PI64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32,
+                                      ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_uint32),
+                                      ctypes.POINTER(ctypes.c_int64))
+SIGNATURES = {
+    "polydet_prime_table": (_I, [_PU32]),
+    "polydet_hadamard_primes": (_I, [_I, _PI64, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "polydet_plan": (_I, [ctypes.POINTER(_VP), _I, _I, _PI32, _I, _U32]),
+    "polydet_plan_destroy": (_I, [_VP]),
+    "polydet_plan_query": (_I, [_VP, ctypes.POINTER(PlanInfo)]),
+    "polydet_plan_primes": (_I, [_VP, _PU32]),
+    "polydet_plan_roots": (_I, [_VP, _PU32]),
+    "polydet_eval": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
+    "polydet_condense_batch": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
+    "polydet_interp": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
+    "polydet_crt": (_I, [_VP, _VP, _VP, _VP]),
+    "polydet_sync_status": (_I, [_VP, _VP, _PU32]),
+    "polydet_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load libpolydet.so (raises if it is missing: no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpolydet.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    if _lib is None:
+        return ""
+    s = _lib.polydet_last_error()
+    return s.decode() if s else ""
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != OK:
+        raise PolydetError(rc, what)
+
+
+def prime_table() -> List[int]:
+    L = lib()
+    n = L.polydet_prime_table(None)
+    buf = (ctypes.c_uint32 * n)()
+    L.polydet_prime_table(buf)
+    return list(buf)
+
+
+def hadamard_primes(entry_l1: np.ndarray) -> tuple[int, float]:
+    """Prime count and log2 of the coefficient bound from [n][n] l1 norms."""
+    l1 = np.ascontiguousarray(entry_l1, dtype=np.int64)
+    n = l1.shape[0]
+    P = ctypes.c_int(0)
+    lb = ctypes.c_double(0)
+    _check(lib().polydet_hadamard_primes(n, l1.ctypes.data_as(_PI64), ctypes.byref(P),
+                                         ctypes.byref(lb)), "polydet_hadamard_primes")
+    return P.value, lb.value
+
+
+def _ptr(t: torch.Tensor, dtype, numel: int, name: str) -> ctypes.c_void_p:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream: Optional[torch.cuda.Stream]) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A polydet plan: n x n matrices in len(degs) variables, entry degree
+    <= degs[v] in x_v, over the first ``nprimes`` primes of the table."""
+
+    def __init__(self, n: int, degs: Sequence[int], nprimes: int):
+        L = lib()
+        d = (ctypes.c_int32 * len(degs))(*[int(x) for x in degs])
+        h = ctypes.c_void_p()
+        _check(L.polydet_plan(ctypes.byref(h), int(n), len(degs), d, int(nprimes), 0), "polydet_plan")
+        self._h = h
+        info = PlanInfo()
+        _check(L.polydet_plan_query(h, ctypes.byref(info)), "polydet_plan_query")
+        self.n, self.k, self.P, self.W = info.n, info.nvars, info.P, info.W
+        self.E, self.G, self.C = info.E, info.G, info.C
+        self.d = tuple(info.d[:self.k])
+        self.D = tuple(info.D[:self.k])
+        self.N = tuple(info.N[:self.k])
+        self.workspace_bytes = info.workspace_bytes
+        pr = (ctypes.c_uint32 * self.P)()
+        _check(L.polydet_plan_primes(h, pr), "polydet_plan_primes")
+        self.primes = list(pr)
+        rt = (ctypes.c_uint32 * (self.P * self.k))()
+        _check(L.polydet_plan_roots(h, rt), "polydet_plan_roots")
+        self.roots = [list(rt[q * self.k:(q + 1) * self.k]) for q in range(self.P)]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().polydet_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- stages ------------------------------------------------------------
+    def eval(self, coeffs: torch.Tensor, lo: int, hi: int, evals: torch.Tensor, stream=None) -> None:
+        n2 = self.n * self.n
+        _check(lib().polydet_eval(self._h, _ptr(coeffs, torch.int32, n2 * self.E, "coeffs"), lo, hi,
+                                  _ptr(evals, torch.int32, (hi - lo) * n2 * self.G, "evals"),
+                                  _stream(stream)), "polydet_eval")
+
+    def condense(self, evals: torch.Tensor, lo: int, hi: int, detvals: torch.Tensor, stream=None) -> None:
+        n2 = self.n * self.n
+        _check(lib().polydet_condense_batch(
+            self._h, _ptr(evals, torch.int32, (hi - lo) * n2 * self.G, "evals"), lo, hi,
+            _ptr(detvals, torch.int32, (hi - lo) * self.G, "detvals"), _stream(stream)),
+            "polydet_condense_batch")
+
+    def interp(self, detvals: torch.Tensor, lo: int, hi: int, residues: torch.Tensor, stream=None) -> None:
+        _check(lib().polydet_interp(
+            self._h, _ptr(detvals, torch.int32, (hi - lo) * self.G, "detvals"), lo, hi,
+            _ptr(residues, torch.int32, (hi - lo) * self.C, "residues"), _stream(stream)),
+            "polydet_interp")
+
+    def crt(self, residues: torch.Tensor, limbs: torch.Tensor, stream=None) -> None:
+        _check(lib().polydet_crt(self._h, _ptr(residues, torch.int32, self.P * self.C, "residues"),
+                                 _ptr(limbs, torch.int32, self.C * self.W, "limbs"), _stream(stream)),
+               "polydet_crt")
+
+    def sync_status(self, stream=None) -> int:
+        st = ctypes.c_uint32(0)
+        rc = lib().polydet_sync_status(self._h, _stream(stream), ctypes.byref(st))
+        if rc not in (OK, EBOUND, ETIMEOUT):
+            _check(rc, "polydet_sync_status")
+        return st.value
+
+
+def limbs_to_ints(limbs: np.ndarray, W: int) -> List[int]:
+    """[C][W] little-endian two's-complement uint32 words -> Python ints."""
+    raw = np.ascontiguousarray(limbs, dtype=np.uint32).reshape(-1, W).astype("<u4").tobytes()
+    step = 4 * W
+    return [int.from_bytes(raw[i:i + step], "little", signed=True) for i in range(0, len(raw), step)]
+
+
+def as_u32(t: torch.Tensor) -> np.ndarray:
+    """Host copy of an int32 device tensor, reinterpreted as uint32."""
+    return t.detach().cpu().numpy().view(np.uint32)

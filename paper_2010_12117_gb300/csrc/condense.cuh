@@ -1,0 +1,140 @@
+// Determinant mod p of one n x n matrix per grid node (Sec. 3.2, Algorithm 3).
+//
+// A team of T consecutive lanes owns one matrix: lane t holds the columns
+// j = t, t + T, t + 2T, ... entirely in registers (n <= 12: one lane per
+// matrix; up to 32: 2, 4 or 8 lanes).  Every index into the register array
+// is a compile-time constant after unrolling, so nothing spills to local
+// memory, and there are no barriers: the team talks through warp shuffles.
+//
+// Elimination is fraction free (the paper's update, Algorithm 3 step (3)):
+// at step c every column j > c of every row i > c becomes
+// a_cc * a_ij - a_ic * a_cj, evaluated with one Montgomery REDC of the two
+// 62-bit products.  Reading every stored value s as the Montgomery form of
+// v = s / R, that update is exactly v_cc v_ij - v_ic v_cj, so with the pivots
+// v_cc of the steps, det(V) = prod_c v_cc / prod_c v_cc^(n-1-c), and the
+// input A = R * V gives det(A) = R^n det(V).  The denominator is accumulated
+// as prod_{c<n-1} Q_c with Q_c = prod_{j<=c} v_jj, and inverted once by
+// Fermat's little theorem at the end, instead of one inverse per step.
+//
+// Pivot search (Algorithm 3, lines 4-7: first nonzero entry): when the
+// pivot a_cc is zero, the first row r > c with a_rc != 0 is added to row c,
+// which leaves the determinant unchanged.  If the column is zero below c the
+// pivot stays 0 and the result is 0, as the paper states.  The search runs
+// only when some lane of the warp needs it.
+#pragma once
+
+#include "common.cuh"
+
+#define PD_FULL 0xffffffffu
+
+// One elimination step c, with c a template parameter so that every index
+// into the register array is a compile-time constant.
+template <int NN, int T, int c>
+struct ElimStep {
+  static constexpr int M = (NN + T - 1) / T;
+  static PD_D void run(uint32_t (&a)[M][NN], int t, uint32_t p, uint32_t pinv, uint32_t &Q,
+                       uint32_t &den) {
+    constexpr int owner = c % T;
+    constexpr int mc = c / T;
+    uint32_t piv = (T == 1) ? a[mc][c] : __shfl_sync(PD_FULL, a[mc][c], owner, T);
+    if (c < NN - 1) {
+      if (__any_sync(PD_FULL, piv == 0u)) {
+        int r = NN;
+#pragma unroll
+        for (int i = NN - 1; i > c; --i)
+          if (a[mc][i] != 0u) r = i;
+        if (T > 1) r = __shfl_sync(PD_FULL, r, owner, T);
+        const bool fix = (piv == 0u) && (r < NN);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int j = t + T * m;
+          if (j >= c && j < NN) {
+            uint32_t add = 0u;
+#pragma unroll
+            for (int i = c + 1; i < NN; ++i) add = (i == r) ? a[m][i] : add;
+            a[m][c] = fix ? addm(a[m][c], add, p) : a[m][c];
+          }
+        }
+        piv = (T == 1) ? a[mc][c] : __shfl_sync(PD_FULL, a[mc][c], owner, T);
+      }
+      uint32_t f[NN];
+#pragma unroll
+      for (int i = c + 1; i < NN; ++i)
+        f[i] = (T == 1) ? a[mc][i] : __shfl_sync(PD_FULL, a[mc][i], owner, T);
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int j = t + T * m;
+        if (j > c && j < NN) {
+          const uint32_t acj = a[m][c];
+#pragma unroll
+          for (int i = c + 1; i < NN; ++i) a[m][i] = mfms(piv, a[m][i], f[i], acj, p, pinv);
+        }
+      }
+      Q = mmul(Q, piv, p, pinv);
+      den = mmul(den, Q, p, pinv);
+      ElimStep<NN, T, c + 1>::run(a, t, p, pinv, Q, den);
+    } else {
+      Q = mmul(Q, piv, p, pinv);
+    }
+  }
+};
+
+template <int NN, int T>
+struct ElimStep<NN, T, NN> {
+  static constexpr int M = (NN + T - 1) / T;
+  static PD_D void run(uint32_t (&)[M][NN], int, uint32_t, uint32_t, uint32_t &, uint32_t &) {}
+};
+
+template <int NN, int T>
+__global__ void __launch_bounds__(128) condense_kernel(const uint32_t *__restrict__ evals,
+                                                       uint32_t *__restrict__ detvals, int64_t G,
+                                                       const ModP *__restrict__ mod,
+                                                       const uint32_t *__restrict__ rn,
+                                                       int prime_lo) {
+  constexpr int M = (NN + T - 1) / T;
+  const int qrel = blockIdx.y;
+  const int q = prime_lo + qrel;
+  const ModP md = mod[q];
+  const uint32_t p = md.p, pinv = md.pinv;
+  const int t = (T == 1) ? 0 : (int)(threadIdx.x % T);
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
+  const bool active = g < G;
+  const int64_t gg = active ? g : (G - 1);
+  const uint32_t *base = evals + (int64_t)qrel * NN * NN * G + gg;
+
+  uint32_t a[M][NN];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = t + T * m;
+#pragma unroll
+    for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? __ldg(base + (int64_t)(i * NN + j) * G) : 0u;
+  }
+
+  uint32_t Q = md.r1, den = md.r1;
+  ElimStep<NN, T, 0>::run(a, t, p, pinv, Q, den);
+  const uint32_t inv = mpow(den, p - 2u, md.r1, p, pinv);
+  uint32_t res = mmul(Q, inv, p, pinv);
+  res = mmul(res, rn[q], p, pinv);
+  if (active && t == 0) detvals[(int64_t)qrel * G + g] = res;
+}
+
+template <int NN>
+struct TeamFor {
+  static constexpr int value = NN <= 12 ? 1 : (NN <= 16 ? 2 : (NN <= 20 ? 4 : 8));
+};
+
+template <int NN>
+static int launch_condense_n(const polydet_plan_s *pl, const uint32_t *evals, int prime_lo,
+                             int nprimes, uint32_t *detvals, cudaStream_t st) {
+  constexpr int T = TeamFor<NN>::value;
+  const int threads = 128;
+  const int64_t teams_per_cta = threads / T;
+  dim3 grid((unsigned)((pl->G + teams_per_cta - 1) / teams_per_cta), (unsigned)nprimes);
+  condense_kernel<NN, T><<<grid, threads, 0, st>>>(evals, detvals, pl->G, pl->d_mod, pl->d_rn, prime_lo);
+  PD_CUDA(cudaGetLastError());
+  return POLYDET_OK;
+}
+
+#define PD_CONDENSE_CASE(NN) \
+  case NN:                   \
+    return launch_condense_n<NN>(pl, evals, prime_lo, nprimes, detvals, st);

@@ -1,0 +1,90 @@
+// Mixed-radix CRT (Sec. 3.4, Algorithm 4): one thread per determinant
+// coefficient, as in the paper.
+//
+// Digits (standard Garner, the reading of the paper's garbled constants):
+//   alpha_0 = x_0,
+//   alpha_i = (x_i - sum_{j<i} alpha_j * (prod_{l<j} p_l mod p_i)) * c_i mod p_i,
+//   c_i = (prod_{l<i} p_l)^-1 mod p_i,
+// so X = sum_i alpha_i prod_{l<i} p_l, evaluated by Horner's rule
+// X = alpha_0 + p_0 (alpha_1 + p_1 (...)) on 32-bit limbs, then lifted to
+// (-M/2, M/2) and stored as W little-endian two's-complement words.
+// The digits and the limbs of a CTA sit in shared memory as [word][thread]
+// so that the output tile [coefficient][W] is written with coalesced stores.
+#include "common.cuh"
+
+__global__ void __launch_bounds__(128) crt_kernel(const uint32_t *__restrict__ res,
+                                                  uint32_t *__restrict__ limbs, int64_t C, int P,
+                                                  int W, const ModP *__restrict__ mod,
+                                                  const uint32_t *__restrict__ garner,
+                                                  const uint32_t *__restrict__ mhalf,
+                                                  const uint32_t *__restrict__ mfull) {
+  extern __shared__ uint32_t sh[];
+  const int bd = blockDim.x, tid = threadIdx.x;
+  uint32_t *alpha = sh;          // [P][bd]
+  uint32_t *X = sh + P * bd;     // [W][bd]
+  const int64_t c0 = (int64_t)blockIdx.x * bd;
+  const int64_t c = c0 + tid;
+  const bool act = c < C;
+
+  for (int i = 0; i < P; ++i) {
+    const ModP m = mod[i];
+    const uint32_t x = act ? res[(int64_t)i * C + c] : 0u;
+    uint32_t acc = 0u;
+    for (int j = 0; j < i; ++j)
+      acc = addm(acc, mmul(alpha[j * bd + tid], __ldg(garner + i * P + j), m.p, m.pinv), m.p);
+    alpha[i * bd + tid] = mmul(subm(x, acc, m.p), __ldg(garner + i * P + i), m.p, m.pinv);
+  }
+
+  for (int w = 0; w < W; ++w) X[w * bd + tid] = 0u;
+  X[tid] = alpha[(P - 1) * bd + tid];
+  for (int i = P - 2; i >= 0; --i) {
+    const uint32_t pi = mod[i].p;
+    uint64_t carry = alpha[i * bd + tid];
+    const int lim = min(W, P - i);
+    for (int w = 0; w < lim; ++w) {
+      const uint64_t t = (uint64_t)X[w * bd + tid] * pi + carry;
+      X[w * bd + tid] = (uint32_t)t;
+      carry = t >> 32;
+    }
+  }
+
+  int cmp = 0;  // compare X with (M - 1) / 2 from the top word down
+  for (int w = W - 1; w >= 0; --w) {
+    const uint32_t xv = X[w * bd + tid], hv = __ldg(mhalf + w);
+    if (cmp == 0) cmp = (xv > hv) ? 1 : ((xv < hv) ? -1 : 0);
+  }
+  if (cmp > 0) {  // X - M
+    uint32_t borrow = 0u;
+    for (int w = 0; w < W; ++w) {
+      const uint64_t t = (uint64_t)X[w * bd + tid] - __ldg(mfull + w) - borrow;
+      X[w * bd + tid] = (uint32_t)t;
+      borrow = (uint32_t)(t >> 63);
+    }
+  }
+  __syncthreads();
+
+  const int64_t ncoef = min((int64_t)bd, C - c0);
+  for (int64_t f = tid; f < ncoef * W; f += bd) {
+    const int64_t cc = f / W;
+    const int w = (int)(f - cc * W);
+    limbs[c0 * W + f] = X[w * bd + cc];
+  }
+}
+
+extern "C" int polydet_crt(polydet_plan_t pl, const uint32_t *residues, uint32_t *limbs,
+                           void *stream) {
+  if (!pl || !residues || !limbs) return POLYDET_EINVAL;
+  const int threads = 128;
+  const size_t smem = (size_t)(pl->P + pl->W) * threads * sizeof(uint32_t);
+  static bool attr_set = false;
+  if (!attr_set) {
+    PD_CUDA(cudaFuncSetAttribute(crt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  const unsigned blocks = (unsigned)((pl->C + threads - 1) / threads);
+  crt_kernel<<<blocks, threads, smem, (cudaStream_t)stream>>>(residues, limbs, pl->C, pl->P, pl->W,
+                                                               pl->d_mod, pl->d_garner, pl->d_mhalf,
+                                                               pl->d_mfull);
+  PD_CUDA(cudaGetLastError());
+  return POLYDET_OK;
+}

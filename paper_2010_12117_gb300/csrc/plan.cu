@@ -1,0 +1,363 @@
+// Host side of libpolydet: the prime table (Eq. 1), the coefficient bound and
+// prime count (Sec. 2), plan construction (grid sizes, roots of unity,
+// twiddles, Montgomery and Garner constants) and status plumbing.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+static char g_err[256] = "";
+
+void pd_set_error(const char *what, cudaError_t e) {
+  snprintf(g_err, sizeof g_err, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" const char *polydet_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------------------
+// Prime table: p = c * 2^20 + 1 in (2^30, 2^31), largest first.  Primality by
+// Miller-Rabin with bases 2, 7, 61 (deterministic below 4,759,123,141).
+// ---------------------------------------------------------------------------
+static bool is_prime_u32(uint32_t n) {
+  if (n < 2) return false;
+  for (uint32_t q : {2u, 3u, 5u, 7u, 11u, 13u, 61u})
+    if (n % q == 0) return n == q;
+  uint32_t d = n - 1;
+  int s = 0;
+  while (!(d & 1)) {
+    d >>= 1;
+    ++s;
+  }
+  for (uint32_t a : {2u, 7u, 61u}) {
+    uint32_t x = h_powmod(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int r = 1; r < s; ++r) {
+      x = h_mulmod(x, x, n);
+      if (x == n - 1) {
+        comp = false;
+        break;
+      }
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+
+static const std::vector<uint32_t> &prime_table() {
+  static std::vector<uint32_t> t;
+  if (t.empty()) {
+    for (uint32_t c = (0x7fffffffu >> 20); c > (0x40000000u >> 20); --c) {
+      uint32_t p = (c << 20) + 1u;
+      if (p > 0x40000000u && p < 0x80000000u && is_prime_u32(p)) t.push_back(p);
+    }
+  }
+  return t;
+}
+
+// Least generator of (Z/pZ)^*: p - 1 = c * 2^20.
+static uint32_t least_generator(uint32_t p) {
+  std::vector<uint32_t> fs;
+  uint32_t m = p - 1;
+  for (uint32_t q = 2; (uint64_t)q * q <= m; ++q) {
+    if (m % q == 0) {
+      fs.push_back(q);
+      while (m % q == 0) m /= q;
+    }
+  }
+  if (m > 1) fs.push_back(m);
+  for (uint32_t g = 2;; ++g) {
+    bool ok = true;
+    for (uint32_t q : fs)
+      if (h_powmod(g, (p - 1) / q, p) == 1) {
+        ok = false;
+        break;
+      }
+    if (ok) return g;
+  }
+}
+
+extern "C" int polydet_prime_table(uint32_t *out) {
+  const auto &t = prime_table();
+  if (out) memcpy(out, t.data(), t.size() * sizeof(uint32_t));
+  return (int)t.size();
+}
+
+extern "C" int polydet_hadamard_primes(int n, const int64_t *entry_l1, int *nprimes_out,
+                                       double *log2_bound_out) {
+  if (n < 1 || n > POLYDET_MAX_N || !entry_l1 || !nprimes_out) return POLYDET_EINVAL;
+  // log2 of prod_i sqrt(sum_j l1^2), rows and columns; the smaller is used.
+  long double lr = 0, lc = 0;
+  bool zero_r = false, zero_c = false;
+  for (int i = 0; i < n; ++i) {
+    long double sr = 0, sc = 0;
+    for (int j = 0; j < n; ++j) {
+      if (entry_l1[i * n + j] < 0 || entry_l1[j * n + i] < 0) return POLYDET_EINVAL;
+      long double a = (long double)entry_l1[i * n + j];
+      long double b = (long double)entry_l1[j * n + i];
+      sr += a * a;
+      sc += b * b;
+    }
+    if (sr == 0) zero_r = true; else lr += 0.5L * log2l(sr);
+    if (sc == 0) zero_c = true; else lc += 0.5L * log2l(sc);
+  }
+  bool zero = zero_r || zero_c;  // a zero row or column: det = 0
+  long double lb = zero ? -1.0L : (lr < lc ? lr : lc);
+  const auto &t = prime_table();
+  long double acc = 0;
+  int P = 0;
+  for (size_t i = 0; i < t.size(); ++i) {
+    acc += log2l((long double)t[i]);
+    if ((int)i + 1 >= 2 && acc > 1.0L + lb + 1e-6L) {
+      P = (int)i + 1;
+      break;
+    }
+  }
+  if (!P) return POLYDET_EPRIMES;
+  *nprimes_out = P;
+  if (log2_bound_out) *log2_bound_out = (double)lb;
+  return POLYDET_OK;
+}
+
+static int pow2_at_least(int64_t x) {
+  int64_t n = 1;
+  while (n < x) n <<= 1;
+  return (int)n;
+}
+
+static void free_plan(polydet_plan_s *pl) {
+  if (!pl) return;
+  cudaFree(pl->d_mod);
+  cudaFree(pl->d_tw_fwd);
+  cudaFree(pl->d_tw_inv);
+  cudaFree(pl->d_ninv);
+  cudaFree(pl->d_rn);
+  cudaFree(pl->d_garner);
+  cudaFree(pl->d_mhalf);
+  cudaFree(pl->d_mfull);
+  cudaFree(pl->d_status);
+  cudaFree(pl->d_ws);
+  delete pl;
+}
+
+template <class T>
+static int upload(T **dst, const std::vector<T> &src) {
+  size_t bytes = src.size() * sizeof(T);
+  if (bytes == 0) bytes = sizeof(T);
+  cudaError_t e = cudaMalloc((void **)dst, bytes);
+  if (e != cudaSuccess) {
+    pd_set_error("cudaMalloc", e);
+    return POLYDET_ENOMEM;
+  }
+  if (!src.empty()) {
+    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      pd_set_error("cudaMemcpy", e);
+      return POLYDET_ECUDA;
+    }
+  }
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
+                            int nprimes, uint32_t flags) {
+  if (!out || n < 1 || n > POLYDET_MAX_N || nvars < 1 || nvars > POLYDET_MAX_VARS ||
+      !entry_deg || flags != 0)
+    return POLYDET_EINVAL;
+  const auto &table = prime_table();
+  if (nprimes < 1) return POLYDET_EINVAL;
+  if (nprimes > (int)table.size()) return POLYDET_EPRIMES;
+
+  polydet_plan_s *pl = new polydet_plan_s();
+  memset(pl, 0, sizeof *pl);
+  pl->n = n;
+  pl->nvars = nvars;
+  pl->P = nprimes;
+  pl->E = 1;
+  pl->G = 1;
+  pl->C = 1;
+  int off = 0;
+  for (int v = 0; v < nvars; ++v) {
+    if (entry_deg[v] < 0) {
+      delete pl;
+      return POLYDET_EINVAL;
+    }
+    pl->d[v] = entry_deg[v];
+    pl->D[v] = n * entry_deg[v];
+    int64_t need = (int64_t)pl->D[v] + 1;
+    if (need > POLYDET_MAX_GRID_DIM) {
+      delete pl;
+      return POLYDET_EDEGREE;
+    }
+    pl->N[v] = pow2_at_least(need);
+    int lg = 0;
+    while ((1 << lg) < pl->N[v]) ++lg;
+    pl->logN[v] = lg;
+    pl->E *= (int64_t)(pl->d[v] + 1);
+    pl->G *= pl->N[v];
+    pl->C *= (int64_t)(pl->D[v] + 1);
+    pl->tw_off[v] = off;
+    off += (pl->N[v] + 1) / 2;
+  }
+  pl->tw_len = off > 0 ? off : 1;
+
+  // Primes, roots, Montgomery constants, twiddles.
+  std::vector<ModP> mod(nprimes);
+  std::vector<uint32_t> twf((size_t)nprimes * pl->tw_len, 0), twi((size_t)nprimes * pl->tw_len, 0);
+  std::vector<uint32_t> ninv((size_t)nprimes * nvars), rn(nprimes);
+  for (int q = 0; q < nprimes; ++q) {
+    uint32_t p = table[q];
+    pl->primes[q] = p;
+    uint32_t inv = 1;  // Newton iteration for p^-1 mod 2^32
+    for (int it = 0; it < 5; ++it) inv *= 2u - p * inv;
+    mod[q].p = p;
+    mod[q].pinv = inv;
+    mod[q].r1 = h_mont(1, p);
+    mod[q].r2 = h_mont(mod[q].r1, p);
+    uint32_t g = least_generator(p);
+    for (int v = 0; v < nvars; ++v) {
+      int N = pl->N[v];
+      uint32_t w = h_powmod(g, (uint64_t)(p - 1) / N, p);
+      uint32_t wi = h_powmod(w, p - 2, p);
+      pl->roots[q][v] = w;
+      uint32_t x = 1, y = 1;
+      for (int j = 0; j < N / 2; ++j) {
+        twf[(size_t)q * pl->tw_len + pl->tw_off[v] + j] = h_mont(x, p);
+        twi[(size_t)q * pl->tw_len + pl->tw_off[v] + j] = h_mont(y, p);
+        x = h_mulmod(x, w, p);
+        y = h_mulmod(y, wi, p);
+      }
+      ninv[(size_t)q * nvars + v] = h_mont(h_powmod(N % p, p - 2, p), p);
+    }
+    rn[q] = h_powmod(mod[q].r1, (uint64_t)n, p);  // (R mod p)^n = R^n mod p
+  }
+
+  // Garner tables (Sec. 3.4 with the standard reading of its constants):
+  // g[i][j] = (prod_{l<j} p_l mod p_i) * R for j < i, g[i][i] = c_i * R with
+  // c_i = (prod_{l<i} p_l)^-1 mod p_i.
+  std::vector<uint32_t> garner((size_t)nprimes * nprimes, 0);
+  for (int i = 0; i < nprimes; ++i) {
+    uint32_t p = table[i];
+    uint32_t m = 1;
+    for (int j = 0; j < i; ++j) {
+      garner[(size_t)i * nprimes + j] = h_mont(m, p);
+      m = h_mulmod(m, table[j] % p, p);
+    }
+    garner[(size_t)i * nprimes + i] = h_mont(h_powmod(m, p - 2, p), p);
+  }
+  // M = prod p as 32-bit limbs; W = ceil(bitlen(M) / 32).
+  std::vector<uint32_t> M(nprimes + 1, 0);
+  M[0] = 1;
+  int used = 1;
+  for (int i = 0; i < nprimes; ++i) {
+    uint64_t carry = 0;
+    for (int w = 0; w < used; ++w) {
+      uint64_t t = (uint64_t)M[w] * table[i] + carry;
+      M[w] = (uint32_t)t;
+      carry = t >> 32;
+    }
+    if (carry) M[used++] = (uint32_t)carry;
+  }
+  pl->W = used;
+  M.resize(used);
+  std::vector<uint32_t> H(used);
+  for (int w = 0; w < used; ++w) {  // (M - 1) / 2; M is odd
+    uint32_t lo = (w == 0) ? (M[0] - 1u) : M[w];
+    uint32_t hi_bit = (w + 1 < used) ? (M[w + 1] & 1u) : 0u;
+    H[w] = (lo >> 1) | (hi_bit << 31);
+  }
+
+  // Workspace (words): evaluation uses it for odd passes, interpolation for
+  // all passes but the last, ping-ponging between two halves.
+  int64_t n2 = (int64_t)n * n;
+  uint64_t eval_ws = 0, interp_ws = 0;
+  for (int v = 1; v < nvars; v += 2) {  // eval pass v output: prod_{u<v} L_u * prod_{u>=v} N_u
+    int64_t s = 1;
+    for (int u = 0; u < nvars; ++u) s *= (u < v) ? (pl->d[u] + 1) : pl->N[u];
+    if ((uint64_t)s > eval_ws) eval_ws = (uint64_t)s;
+  }
+  eval_ws *= (uint64_t)n2 * nprimes;
+  for (int v = 1; v < nvars; ++v) {  // interp pass v output: prod_{u<v} N_u * prod_{u>=v} (D_u+1)
+    int64_t s = 1;
+    for (int u = 0; u < nvars; ++u) s *= (u < v) ? pl->N[u] : (pl->D[u] + 1);
+    if ((uint64_t)s > interp_ws) interp_ws = (uint64_t)s;
+  }
+  interp_ws *= 2ull * nprimes;
+  pl->ws_words = eval_ws > interp_ws ? eval_ws : interp_ws;
+
+  int rc;
+  if ((rc = upload(&pl->d_mod, mod)) || (rc = upload(&pl->d_tw_fwd, twf)) ||
+      (rc = upload(&pl->d_tw_inv, twi)) || (rc = upload(&pl->d_ninv, ninv)) ||
+      (rc = upload(&pl->d_rn, rn)) || (rc = upload(&pl->d_garner, garner)) ||
+      (rc = upload(&pl->d_mhalf, H)) || (rc = upload(&pl->d_mfull, M)) ||
+      (rc = upload(&pl->d_status, std::vector<uint32_t>(1, 0u)))) {
+    free_plan(pl);
+    return rc;
+  }
+  if (pl->ws_words) {
+    cudaError_t e = cudaMalloc((void **)&pl->d_ws, pl->ws_words * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+      pd_set_error("cudaMalloc(workspace)", e);
+      free_plan(pl);
+      return POLYDET_ENOMEM;
+    }
+  }
+  *out = pl;
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_plan_destroy(polydet_plan_t plan) {
+  if (!plan) return POLYDET_EINVAL;
+  free_plan(plan);
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_plan_query(polydet_plan_t pl, polydet_plan_info *info) {
+  if (!pl || !info) return POLYDET_EINVAL;
+  memset(info, 0, sizeof *info);
+  info->n = pl->n;
+  info->nvars = pl->nvars;
+  info->P = pl->P;
+  info->W = pl->W;
+  info->E = pl->E;
+  info->G = pl->G;
+  info->C = pl->C;
+  for (int v = 0; v < pl->nvars; ++v) {
+    info->d[v] = pl->d[v];
+    info->D[v] = pl->D[v];
+    info->N[v] = pl->N[v];
+  }
+  info->workspace_bytes = pl->ws_words * sizeof(uint32_t);
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_plan_primes(polydet_plan_t pl, uint32_t *primes_out) {
+  if (!pl || !primes_out) return POLYDET_EINVAL;
+  memcpy(primes_out, pl->primes, pl->P * sizeof(uint32_t));
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_plan_roots(polydet_plan_t pl, uint32_t *roots_out) {
+  if (!pl || !roots_out) return POLYDET_EINVAL;
+  for (int q = 0; q < pl->P; ++q)
+    for (int v = 0; v < pl->nvars; ++v) roots_out[q * pl->nvars + v] = pl->roots[q][v];
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_sync_status(polydet_plan_t pl, void *stream, uint32_t *status_out) {
+  if (!pl) return POLYDET_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t s = 0;
+  PD_CUDA(cudaMemcpyAsync(&s, pl->d_status, sizeof s, cudaMemcpyDeviceToHost, st));
+  PD_CUDA(cudaStreamSynchronize(st));
+  PD_CUDA(cudaMemsetAsync(pl->d_status, 0, sizeof(uint32_t), st));
+  PD_CUDA(cudaStreamSynchronize(st));
+  if (status_out) *status_out = s;
+  if (s & POLYDET_STATUS_TIMEOUT) return POLYDET_ETIMEOUT;
+  if (s & POLYDET_STATUS_BOUND) return POLYDET_EBOUND;
+  return POLYDET_OK;
+}

@@ -1,0 +1,79 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+declared in include/polydet.h, the binding covers them, and the host-only
+planning calls agree with the oracle's independent versions."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from helpers import ROOT, ensure_lib
+from oracle import modular, plan as oplan
+
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+           if f.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(polydet_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = ensure_lib()
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(L, name), f"{name} declared but not exported"
+    from paper_2010_12117_gb300 import binding
+    nm = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True)
+    exported = set(re.findall(r"\bpolydet_[a-z0-9_]+\b", nm.stdout))
+    assert set(names) <= exported
+
+
+def test_binding_covers_the_header():
+    from paper_2010_12117_gb300 import binding
+    assert set(declared_functions()) <= set(binding.SIGNATURES)
+
+
+def test_prime_table_matches_oracle():
+    ensure_lib()
+    from paper_2010_12117_gb300 import binding
+    assert binding.prime_table() == modular.ntt_primes()
+
+
+def _l1_from_bits(rng, n, bits):
+    return rng.integers(0, 2 ** bits, (n, n), dtype=np.int64)
+
+
+@pytest.mark.parametrize("n,bits", [(1, 5), (4, 8), (12, 20), (16, 30), (24, 22), (32, 25)])
+def test_hadamard_prime_count_matches_oracle(n, bits):
+    ensure_lib()
+    from paper_2010_12117_gb300 import binding
+    rng = np.random.default_rng(n * 100 + bits)
+    for _ in range(5):
+        l1 = _l1_from_bits(rng, n, bits)
+        # an integer matrix with these l1 norms (constants) has the same bound
+        coeffs = l1.reshape(n, n, 1).tolist()
+        want = oplan.primes_needed(oplan.hadamard_bound_sq(coeffs, (0,)), modular.ntt_primes())
+        got, _ = binding.hadamard_primes(l1)
+        # the library works in floating point with a 1e-6-bit safety margin: it
+        # may take one prime more than the exact rule, never fewer
+        assert got in (want, want + 1)
+
+
+def test_hadamard_zero_matrix_and_errors():
+    ensure_lib()
+    from paper_2010_12117_gb300 import binding
+    P, lb = binding.hadamard_primes(np.zeros((3, 3), dtype=np.int64))
+    assert P == 2
+    L = binding.lib()
+    out = ctypes.c_int(0)
+    assert L.polydet_hadamard_primes(0, None, ctypes.byref(out), None) == binding.EINVAL

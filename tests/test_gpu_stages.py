@@ -1,0 +1,235 @@
+"""Stage-by-stage parity of the CUDA kernels with the CPU oracle, through the
+C ABI.  Integer work: every comparison is bit-exact."""
+import random
+from math import prod
+
+import numpy as np
+import pytest
+
+from helpers import ensure_lib, evals_tensor, random_residue_mats
+from oracle import modular, plan as oplan
+from paper_2010_12117_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_lib()
+
+
+def Plan(n, degs, P):
+    from paper_2010_12117_gb300.binding import Plan as _P
+    return _P(n, degs, P)
+
+
+def u32(t):
+    from paper_2010_12117_gb300.binding import as_u32
+    return as_u32(t)
+
+
+def test_plan_constants_match_oracle():
+    pl = Plan(12, (3, 3, 3), 5)
+    assert pl.primes == modular.ntt_primes()[:5]
+    assert pl.D == (36, 36, 36) and pl.N == (64, 64, 64)
+    assert pl.G == 64 ** 3 and pl.C == 37 ** 3 and pl.E == 64
+    for q, p in enumerate(pl.primes):
+        for v, N in enumerate(pl.N):
+            assert pl.roots[q][v] == modular.root_of_unity(p, N)
+    assert pl.W == oplan.output_words(pl.primes)
+
+
+@pytest.mark.parametrize("n,degs,P,sample", [
+    (4, (2, 2), 2, None),          # dense 4x4 workload, every node
+    (3, (2, 0, 1), 2, None),       # a variable of degree 0 (N_v = 1)
+    (16, (6,), 3, None),           # Sylvester-sized univariate
+    (5, (3, 1, 2), 2, 300),        # trivariate, sampled nodes
+    (12, (3, 3, 3), 1, 40),        # 12x12 trivariate grid (64^3), sampled
+])
+def test_eval_matches_direct_evaluation(n, degs, P, sample):
+    rng = np.random.default_rng(n + 7 * P)
+    pm = synth.random_matrix(rng, n, degs, 0.7, -(2 ** 31), 2 ** 31)
+    pm.coeffs[0, 0, 0] = -(2 ** 31)  # extreme int32 values
+    pm.coeffs[0, 0, -1] = 2 ** 31 - 1
+    pl = Plan(n, degs, P)
+    coeffs = torch.from_numpy(pm.coeffs.astype(np.int32).reshape(-1)).cuda()
+    evals = torch.empty(P * n * n * pl.G, dtype=torch.int32, device="cuda")
+    pl.eval(coeffs, 0, P, evals)
+    torch.cuda.synchronize()
+    got = u32(evals).reshape(P, n * n, pl.G)
+    nodes = range(pl.G) if sample is None else sorted(set(
+        [0, pl.G - 1] + [int(x) for x in rng.integers(0, pl.G, sample)]))
+    entries = range(n * n) if n * n <= 16 or sample is None else \
+        sorted(set([0, n * n - 1] + [int(x) for x in rng.integers(0, n * n, 12)]))
+    for q in range(P):
+        p = pl.primes[q]
+        ws = pl.roots[q]
+        for e in entries:
+            vec = pm.coeffs.reshape(n * n, -1)[e].tolist()
+            for g in nodes:
+                idx = modular.grid_index(g, pl.N)
+                assert int(got[q, e, g]) == modular.eval_point(vec, degs, idx, ws, p), (q, e, g)
+
+
+def test_eval_prime_range_offsets():
+    """A range [lo, hi) writes slot 0 for prime lo."""
+    n, degs = 4, (2, 2)
+    rng = np.random.default_rng(3)
+    pm = synth.random_matrix(rng, n, degs, 1.0, -10, 11)
+    pl = Plan(n, degs, 4)
+    coeffs = torch.from_numpy(pm.coeffs.astype(np.int32).reshape(-1)).cuda()
+    full = torch.empty(4 * n * n * pl.G, dtype=torch.int32, device="cuda")
+    part = torch.empty(2 * n * n * pl.G, dtype=torch.int32, device="cuda")
+    pl.eval(coeffs, 0, 4, full)
+    pl.eval(coeffs, 2, 4, part)
+    torch.cuda.synchronize()
+    assert np.array_equal(u32(full)[2 * n * n * pl.G:], u32(part))
+
+
+def _special_matrices(n, p, rng):
+    """Matrices that force the pivot search or are singular."""
+    mats = []
+    I = np.eye(n, dtype=np.uint64)
+    mats.append(I)                                   # identity
+    perm = np.eye(n, dtype=np.uint64)[rng.permutation(n)]
+    mats.append(perm)                                # permutation: every pivot searched
+    z = np.zeros((n, n), dtype=np.uint64)
+    mats.append(z)                                   # zero matrix
+    r = rng.integers(0, p, (n, n), dtype=np.uint64)
+    if n > 1:
+        r2 = r.copy()
+        r2[n - 1] = r2[0]
+        mats.append(r2)                              # duplicate row: det 0
+        r3 = r.copy()
+        r3[:, 0] = 0
+        r3[n - 1, 0] = 5
+        mats.append(r3)                              # only the last row can pivot column 0
+        r4 = r.copy()
+        r4[: n // 2, : n // 2] = 0
+        mats.append(r4)                              # zero leading block
+        r5 = np.triu(r)
+        mats.append(r5)                              # triangular
+        r6 = r.copy()
+        r6[:, n // 2] = 0
+        mats.append(r6)                              # zero column: det 0
+    mats.append(np.full((n, n), p - 1, dtype=np.uint64))  # all -1: rank 1
+    return mats
+
+
+@pytest.mark.parametrize("n", list(range(1, 33)))
+def test_condense_matches_gaussian_elimination(n):
+    """Every matrix order 1..32 (each kernel instantiation), random residues,
+    sparse residues and matrices that need the pivot search."""
+    rng = np.random.default_rng(500 + n)
+    d = max(1, 128 // n)  # G between 128 and 512 nodes
+    P = 2
+    pl = Plan(n, (d,), P)
+    G = pl.G
+    mats = random_residue_mats(rng, P, G, n, pl.primes)
+    # sparse residues in a quarter of the nodes
+    for q in range(P):
+        sp = random_residue_mats(rng, 1, G // 4, n, pl.primes[q:q + 1], zero_frac=0.6)[0]
+        mats[q, : G // 4] = sp
+        for s, M in enumerate(_special_matrices(n, pl.primes[q], rng)):
+            mats[q, G // 4 + s] = M % pl.primes[q]
+    evals = evals_tensor(mats, G)
+    det = torch.empty(P * G, dtype=torch.int32, device="cuda")
+    pl.condense(evals, 0, P, det)
+    torch.cuda.synchronize()
+    got = u32(det).reshape(P, G)
+    check = sorted(set(range(0, G // 4, max(1, G // 64))) | set(range(G // 4, G // 4 + 12)) |
+                   set(int(x) for x in rng.integers(0, G, 24)) | {G - 1})
+    if n <= 6:
+        check = range(G)
+    for q in range(P):
+        p = pl.primes[q]
+        for g in check:
+            want = modular.det_mod_p(mats[q, g].astype(object).tolist(), p)
+            assert int(got[q, g]) == want, (n, q, g)
+
+
+def test_interp_round_trip_against_oracle():
+    """Interpolation of the oracle's evaluations of a random polynomial of
+    bounded degree returns its coefficients, with a clean status."""
+    n, degs, P = 4, (2, 2), 2
+    pl = Plan(n, degs, P)
+    rng = random.Random(17)
+    det_vals = np.empty((P, pl.G), dtype=np.uint64)
+    want = []
+    for q in range(P):
+        p = pl.primes[q]
+        vec = [rng.randrange(p) for _ in range(pl.C)]
+        want.append(vec)
+        det_vals[q] = modular.eval_grid(vec, pl.D, pl.N, pl.roots[q], p)
+    dv = torch.from_numpy(det_vals.astype(np.uint32).view(np.int32).reshape(-1)).cuda()
+    res = torch.empty(P * pl.C, dtype=torch.int32, device="cuda")
+    pl.interp(dv, 0, P, res)
+    assert pl.sync_status() == 0
+    got = u32(res).reshape(P, pl.C)
+    for q in range(P):
+        assert got[q].tolist() == want[q]
+    # and against the oracle's inverse DFT directly
+    box, clean = modular.interp_grid(det_vals[0].tolist(), pl.N, pl.roots[0], pl.primes[0], pl.D)
+    assert clean and box == want[0]
+
+
+def test_interp_flags_a_degree_bound_violation():
+    """Values that are not those of a polynomial within the box leave a
+    nonzero tail: the status word reports it (no fault, no abort)."""
+    from paper_2010_12117_gb300.binding import EBOUND, lib
+    n, degs, P = 2, (1, 1), 1  # D = (2, 2) inside the 4 x 4 grid: a 7-value tail
+    pl = Plan(n, degs, P)
+    assert pl.C < pl.G
+    rng = np.random.default_rng(5)
+    vals = rng.integers(0, pl.primes[0], pl.G, dtype=np.uint64).astype(np.uint32)
+    dv = torch.from_numpy(vals.view(np.int32)).cuda()
+    res = torch.empty(pl.C, dtype=torch.int32, device="cuda")
+    pl.interp(dv, 0, 1, res)
+    assert pl.sync_status() & 1
+    assert pl.sync_status() == 0  # reading clears it
+    # the kept coefficients still equal the oracle's inverse DFT of those values
+    box, clean = modular.interp_grid(vals.tolist(), pl.N, pl.roots[0], pl.primes[0], pl.D)
+    assert not clean and u32(res).tolist() == box
+
+
+@pytest.mark.parametrize("P", [1, 2, 5, 11, 20, 24, 40, 91])
+def test_crt_matches_garner(P):
+    d = 700 if P < 40 else 120  # C = d + 1: not a multiple of the CTA size
+    pl = Plan(1, (d,), P)
+    C = pl.C
+    rng = random.Random(P)
+    M = prod(pl.primes)
+    xs = [rng.randrange(-(M // 2), M // 2 + 1) for _ in range(C)]
+    for j, X in enumerate([0, 1, -1, M // 2, -(M // 2), M // 2 - 1, -(M // 2) + 1]):
+        xs[j] = X
+    res = np.array([[X % p for X in xs] for p in pl.primes], dtype=np.uint64).astype(np.uint32)
+    rd = torch.from_numpy(res.view(np.int32).reshape(-1)).cuda()
+    limbs = torch.empty(C * pl.W, dtype=torch.int32, device="cuda")
+    pl.crt(rd, limbs)
+    torch.cuda.synchronize()
+    from paper_2010_12117_gb300.binding import limbs_to_ints
+    got = limbs_to_ints(u32(limbs).reshape(C, pl.W), pl.W)
+    for j in range(C):
+        assert got[j] == modular.garner(res[:, j].tolist(), pl.primes) == xs[j], j
+    # the raw words are the oracle's two's complement limbs
+    assert u32(limbs).reshape(C, pl.W)[3].tolist() == modular.to_limbs(xs[3], pl.W)
+
+
+def test_invalid_arguments_are_rejected():
+    from paper_2010_12117_gb300.binding import EINVAL, PolydetError
+    pl = Plan(4, (2, 2), 2)
+    buf = torch.empty(16, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        pl.eval(buf, 0, 2, buf)  # too small
+    big = torch.empty(4 * 16 * pl.G, dtype=torch.int32, device="cuda")
+    with pytest.raises(PolydetError) as ei:
+        pl.condense(big, 1, 1, big)  # empty range
+    assert ei.value.code == EINVAL
+    with pytest.raises(PolydetError):
+        pl.interp(big, 0, 3, big)  # beyond P
+    with pytest.raises(PolydetError):
+        Plan(33, (1,), 2)
+    with pytest.raises(PolydetError):
+        Plan(4, (3000,), 2)  # N_v beyond 8192
