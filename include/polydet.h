@@ -73,7 +73,8 @@ typedef struct polydet_plan_info {
   int32_t d[POLYDET_MAX_VARS];     /* entry degree bound per variable      */
   int32_t D[POLYDET_MAX_VARS];     /* determinant degree bound, n * d_v    */
   int32_t N[POLYDET_MAX_VARS];     /* grid size per variable               */
-  uint64_t workspace_bytes;        /* device scratch owned by the plan     */
+  uint64_t eval_ws_words;          /* polydet_eval scratch per prime       */
+  uint64_t interp_ws_words;        /* polydet_interp scratch per prime     */
 } polydet_plan_info;
 
 /* Primes of Eq. 1 with q = 20: every p = c * 2^20 + 1 in (2^30, 2^31), largest
@@ -93,10 +94,10 @@ int polydet_hadamard_primes(int n, const int64_t *entry_l1, int *nprimes_out,
 
 /* Build a plan for n x n matrices in `nvars` variables whose entries have
  * degree <= entry_deg[v] (host array) in x_v, using the first `nprimes`
- * primes of the table (must be >= 1).  Allocates the plan's device tables
- * (Montgomery constants, twiddles, Garner tables) and its workspace; later
- * calls allocate nothing.  `flags` must be 0.  The plan must be destroyed
- * with polydet_plan_destroy. */
+ * primes of the table (must be >= 1).  Allocates the plan's small device
+ * tables (Montgomery constants, twiddles, Garner tables, status word); no
+ * later call allocates device memory: scratch is passed in by the caller.
+ * `flags` must be 0.  The plan must be destroyed with polydet_plan_destroy. */
 int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
                  int nprimes, uint32_t flags);
 int polydet_plan_destroy(polydet_plan_t plan);
@@ -109,9 +110,11 @@ int polydet_plan_roots(polydet_plan_t plan, uint32_t *roots_out);
  * [prime_lo, prime_hi) and entry e, the multivariate NTT of the zero-padded
  * coefficients, i.e. the entry at every grid node mod p_q.
  * coeffs_dev: device int32 [n*n][E] (|c| < 2^31).  evals_dev: device uint32
- * [prime_hi - prime_lo][n*n][G]. */
+ * [prime_hi - prime_lo][n*n][G].  ws_dev: device scratch of
+ * (prime_hi - prime_lo) * info.eval_ws_words words (NULL allowed when that
+ * is 0, e.g. for one variable). */
 int polydet_eval(polydet_plan_t plan, const int32_t *coeffs_dev, int prime_lo,
-                 int prime_hi, uint32_t *evals_dev, void *stream);
+                 int prime_hi, uint32_t *evals_dev, uint32_t *ws_dev, void *stream);
 
 /* Stage 2, condensation (Sec. 3.2, Algorithm 3): det of the n x n matrix at
  * every grid node mod p_q, by fraction-free elimination with a search for the
@@ -125,10 +128,12 @@ int polydet_condense_batch(polydet_plan_t plan, const uint32_t *evals_dev,
  * keeping the C coefficients with e_v <= D_v.  Any nonzero coefficient with
  * e_v > D_v sets POLYDET_STATUS_BOUND.  detvals_dev: device uint32
  * [prime_hi - prime_lo][G] (read only); residues_dev: device uint32
- * [prime_hi - prime_lo][C].  These per-prime residues are the restart point
- * of a run (Sec. 4.3): a resumed run recomputes only the missing primes. */
+ * [prime_hi - prime_lo][C]; ws_dev: device scratch of
+ * (prime_hi - prime_lo) * info.interp_ws_words words (NULL allowed when 0).
+ * These per-prime residues are the restart point of a run (Sec. 4.3): a
+ * resumed run recomputes only the missing primes. */
 int polydet_interp(polydet_plan_t plan, const uint32_t *detvals_dev, int prime_lo,
-                   int prime_hi, uint32_t *residues_dev, void *stream);
+                   int prime_hi, uint32_t *residues_dev, uint32_t *ws_dev, void *stream);
 
 /* Stage 4, CRT (Sec. 3.4, Algorithm 4): mixed-radix (Garner) digits of each
  * coefficient over all P primes, converted to the signed integer in
@@ -140,6 +145,13 @@ int polydet_crt(polydet_plan_t plan, const uint32_t *residues_dev, uint32_t *lim
 /* Synchronise `stream`, return the plan's status word in *status_out and clear
  * it.  Returns POLYDET_EBOUND / POLYDET_ETIMEOUT if the matching bit was set. */
 int polydet_sync_status(polydet_plan_t plan, void *stream, uint32_t *status_out);
+
+/* Measurement utility (not a stage of the method): runs two in-register
+ * integer streams on every SM and reports their rates, the ceilings of the
+ * condensation kernels - plain 32-bit multiply-adds per second, and fused
+ * modular updates (a*b - c*d)/2^32 mod p per second.  Allocates and frees a
+ * small buffer; synchronises `stream`. */
+int polydet_probe_int_peaks(void *stream, double *imad_per_s, double *update_per_s);
 
 /* Last CUDA error string seen by the library (host, static storage). */
 const char *polydet_last_error(void);

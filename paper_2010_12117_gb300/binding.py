@@ -35,7 +35,7 @@ class PlanInfo(ctypes.Structure):
                 ("W", ctypes.c_int32), ("E", ctypes.c_int64), ("G", ctypes.c_int64),
                 ("C", ctypes.c_int64), ("d", ctypes.c_int32 * MAX_VARS),
                 ("D", ctypes.c_int32 * MAX_VARS), ("N", ctypes.c_int32 * MAX_VARS),
-                ("workspace_bytes", ctypes.c_uint64)]
+                ("eval_ws_words", ctypes.c_uint64), ("interp_ws_words", ctypes.c_uint64)]
 
 
 _lib = None
@@ -54,11 +54,13 @@ SIGNATURES = {
     "polydet_plan_query": (_I, [_VP, ctypes.POINTER(PlanInfo)]),
     "polydet_plan_primes": (_I, [_VP, _PU32]),
     "polydet_plan_roots": (_I, [_VP, _PU32]),
-    "polydet_eval": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
+    "polydet_eval": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP]),
     "polydet_condense_batch": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
-    "polydet_interp": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
+    "polydet_interp": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP]),
     "polydet_crt": (_I, [_VP, _VP, _VP, _VP]),
     "polydet_sync_status": (_I, [_VP, _VP, _PU32]),
+    "polydet_probe_int_peaks": (_I, [_VP, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
     "polydet_last_error": (ctypes.c_char_p, []),
 }
 
@@ -143,7 +145,8 @@ class Plan:
         self.d = tuple(info.d[:self.k])
         self.D = tuple(info.D[:self.k])
         self.N = tuple(info.N[:self.k])
-        self.workspace_bytes = info.workspace_bytes
+        self.eval_ws_words = int(info.eval_ws_words)
+        self.interp_ws_words = int(info.interp_ws_words)
         pr = (ctypes.c_uint32 * self.P)()
         _check(L.polydet_plan_primes(h, pr), "polydet_plan_primes")
         self.primes = list(pr)
@@ -169,10 +172,24 @@ class Plan:
         self.close()
 
     # -- stages ------------------------------------------------------------
-    def eval(self, coeffs: torch.Tensor, lo: int, hi: int, evals: torch.Tensor, stream=None) -> None:
+    def workspace(self, nprimes: int, device="cuda") -> torch.Tensor:
+        """Scratch for eval/interp over ``nprimes`` primes at a time."""
+        words = max(self.eval_ws_words, self.interp_ws_words, 1) * nprimes
+        return torch.empty(words, dtype=torch.int32, device=device)
+
+    def _ws(self, ws: Optional[torch.Tensor], per_prime: int, np_: int, what: str):
+        if per_prime == 0:
+            return ctypes.c_void_p(ws.data_ptr() if ws is not None else 0)
+        if ws is None:
+            raise ValueError(f"{what} needs a workspace of {per_prime} words per prime")
+        return _ptr(ws, torch.int32, per_prime * np_, "workspace")
+
+    def eval(self, coeffs: torch.Tensor, lo: int, hi: int, evals: torch.Tensor,
+             ws: Optional[torch.Tensor] = None, stream=None) -> None:
         n2 = self.n * self.n
         _check(lib().polydet_eval(self._h, _ptr(coeffs, torch.int32, n2 * self.E, "coeffs"), lo, hi,
                                   _ptr(evals, torch.int32, (hi - lo) * n2 * self.G, "evals"),
+                                  self._ws(ws, self.eval_ws_words, hi - lo, "polydet_eval"),
                                   _stream(stream)), "polydet_eval")
 
     def condense(self, evals: torch.Tensor, lo: int, hi: int, detvals: torch.Tensor, stream=None) -> None:
@@ -182,10 +199,12 @@ class Plan:
             _ptr(detvals, torch.int32, (hi - lo) * self.G, "detvals"), _stream(stream)),
             "polydet_condense_batch")
 
-    def interp(self, detvals: torch.Tensor, lo: int, hi: int, residues: torch.Tensor, stream=None) -> None:
+    def interp(self, detvals: torch.Tensor, lo: int, hi: int, residues: torch.Tensor,
+               ws: Optional[torch.Tensor] = None, stream=None) -> None:
         _check(lib().polydet_interp(
             self._h, _ptr(detvals, torch.int32, (hi - lo) * self.G, "detvals"), lo, hi,
-            _ptr(residues, torch.int32, (hi - lo) * self.C, "residues"), _stream(stream)),
+            _ptr(residues, torch.int32, (hi - lo) * self.C, "residues"),
+            self._ws(ws, self.interp_ws_words, hi - lo, "polydet_interp"), _stream(stream)),
             "polydet_interp")
 
     def crt(self, residues: torch.Tensor, limbs: torch.Tensor, stream=None) -> None:
@@ -199,6 +218,16 @@ class Plan:
         if rc not in (OK, EBOUND, ETIMEOUT):
             _check(rc, "polydet_sync_status")
         return st.value
+
+
+def probe_int_peaks(stream=None) -> tuple[float, float]:
+    """(32-bit multiply-adds per second, fused modular updates per second)
+    measured on the current device by the library's probe kernels."""
+    a = ctypes.c_double(0)
+    u = ctypes.c_double(0)
+    _check(lib().polydet_probe_int_peaks(_stream(stream), ctypes.byref(a), ctypes.byref(u)),
+           "polydet_probe_int_peaks")
+    return a.value, u.value
 
 
 def limbs_to_ints(limbs: np.ndarray, W: int) -> List[int]:

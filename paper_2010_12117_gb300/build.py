@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libpolydet.so")
 
-SOURCES = ["plan.cu", "ntt.cu", "crt.cu", "condense_a.cu", "condense_b.cu",
+SOURCES = ["plan.cu", "ntt.cu", "crt.cu", "probe.cu", "condense_a.cu", "condense_b.cu",
            "condense_c.cu", "condense_d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

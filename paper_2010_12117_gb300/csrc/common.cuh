@@ -116,8 +116,8 @@ struct polydet_plan_s {
   uint32_t *d_mhalf;      // [W] (M-1)/2
   uint32_t *d_mfull;      // [W] M
   uint32_t *d_status;     // 1 word
-  uint32_t *d_ws;         // workspace
-  uint64_t ws_words;
+  uint64_t eval_ws_words;   // caller scratch per prime for polydet_eval
+  uint64_t interp_ws_words; // caller scratch per prime for polydet_interp
   int tw_off[POLYDET_MAX_VARS];
 };
 

@@ -145,33 +145,14 @@ static int check_range(const polydet_plan_s *pl, int lo, int hi) {
   return (pl && lo >= 0 && hi <= pl->P && lo < hi) ? POLYDET_OK : POLYDET_EINVAL;
 }
 
-static uint64_t eval_slot(const polydet_plan_s *pl) {
-  uint64_t best = 0;
-  for (int v = 1; v < pl->nvars; v += 2) {
-    uint64_t s = 1;
-    for (int u = 0; u < pl->nvars; ++u) s *= (u < v) ? (uint64_t)(pl->d[u] + 1) : (uint64_t)pl->N[u];
-    if (s > best) best = s;
-  }
-  return best;
-}
-
-static uint64_t interp_slot(const polydet_plan_s *pl) {
-  uint64_t best = 0;
-  for (int v = 1; v < pl->nvars; ++v) {
-    uint64_t s = 1;
-    for (int u = 0; u < pl->nvars; ++u) s *= (u < v) ? (uint64_t)pl->N[u] : (uint64_t)(pl->D[u] + 1);
-    if (s > best) best = s;
-  }
-  return best;
-}
-
 extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, int hi,
-                            uint32_t *evals, void *stream) {
+                            uint32_t *evals, uint32_t *ws, void *stream) {
   if (check_range(pl, lo, hi) || !coeffs || !evals) return POLYDET_EINVAL;
+  if (pl->eval_ws_words && !ws) return POLYDET_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const int k = pl->nvars, np = hi - lo;
   const int64_t n2 = (int64_t)pl->n * pl->n;
-  const uint64_t slot = eval_slot(pl);
+  const uint64_t slot = n2 ? pl->eval_ws_words / (uint64_t)n2 : 0;
   const void *cur_in = coeffs;
   int64_t cur_item = pl->E, cur_prime = 0;
   int cur_i32 = 1;
@@ -193,7 +174,7 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
       a.out = evals;
       a.out_item_stride = pl->G;
     } else {
-      a.out = pl->d_ws;
+      a.out = ws;
       a.out_item_stride = (int64_t)slot;
     }
     a.out_prime_stride = n2 * a.out_item_stride;
@@ -218,11 +199,12 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
 }
 
 extern "C" int polydet_interp(polydet_plan_t pl, const uint32_t *detvals, int lo, int hi,
-                              uint32_t *residues, void *stream) {
+                              uint32_t *residues, uint32_t *ws, void *stream) {
   if (check_range(pl, lo, hi) || !detvals || !residues) return POLYDET_EINVAL;
+  if (pl->interp_ws_words && !ws) return POLYDET_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const int k = pl->nvars, np = hi - lo;
-  const uint64_t slot = interp_slot(pl);
+  const uint64_t slot = pl->interp_ws_words / 2;
   const void *cur_in = detvals;
   int64_t cur_prime = pl->G;
   int t = 0;
@@ -244,7 +226,7 @@ extern "C" int polydet_interp(polydet_plan_t pl, const uint32_t *detvals, int lo
       a.out = residues;
       a.out_prime_stride = pl->C;
     } else {
-      a.out = pl->d_ws + (uint64_t)(t % 2) * slot * (uint64_t)pl->P;
+      a.out = ws + (uint64_t)(t % 2) * slot * (uint64_t)np;
       a.out_prime_stride = (int64_t)slot;
     }
     a.out_item_stride = 0;

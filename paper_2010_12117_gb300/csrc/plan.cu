@@ -140,7 +140,6 @@ static void free_plan(polydet_plan_s *pl) {
   cudaFree(pl->d_mhalf);
   cudaFree(pl->d_mfull);
   cudaFree(pl->d_status);
-  cudaFree(pl->d_ws);
   delete pl;
 }
 
@@ -271,23 +270,22 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
     H[w] = (lo >> 1) | (hi_bit << 31);
   }
 
-  // Workspace (words): evaluation uses it for odd passes, interpolation for
-  // all passes but the last, ping-ponging between two halves.
+  // Caller scratch per prime (words): evaluation keeps its odd passes there,
+  // interpolation all passes but the last, ping-ponging between two halves.
   int64_t n2 = (int64_t)n * n;
-  uint64_t eval_ws = 0, interp_ws = 0;
+  uint64_t eval_slot = 0, interp_slot = 0;
   for (int v = 1; v < nvars; v += 2) {  // eval pass v output: prod_{u<v} L_u * prod_{u>=v} N_u
-    int64_t s = 1;
-    for (int u = 0; u < nvars; ++u) s *= (u < v) ? (pl->d[u] + 1) : pl->N[u];
-    if ((uint64_t)s > eval_ws) eval_ws = (uint64_t)s;
+    uint64_t s = 1;
+    for (int u = 0; u < nvars; ++u) s *= (u < v) ? (uint64_t)(pl->d[u] + 1) : (uint64_t)pl->N[u];
+    if (s > eval_slot) eval_slot = s;
   }
-  eval_ws *= (uint64_t)n2 * nprimes;
   for (int v = 1; v < nvars; ++v) {  // interp pass v output: prod_{u<v} N_u * prod_{u>=v} (D_u+1)
-    int64_t s = 1;
-    for (int u = 0; u < nvars; ++u) s *= (u < v) ? pl->N[u] : (pl->D[u] + 1);
-    if ((uint64_t)s > interp_ws) interp_ws = (uint64_t)s;
+    uint64_t s = 1;
+    for (int u = 0; u < nvars; ++u) s *= (u < v) ? (uint64_t)pl->N[u] : (uint64_t)(pl->D[u] + 1);
+    if (s > interp_slot) interp_slot = s;
   }
-  interp_ws *= 2ull * nprimes;
-  pl->ws_words = eval_ws > interp_ws ? eval_ws : interp_ws;
+  pl->eval_ws_words = eval_slot * (uint64_t)n2;
+  pl->interp_ws_words = 2 * interp_slot;
 
   int rc;
   if ((rc = upload(&pl->d_mod, mod)) || (rc = upload(&pl->d_tw_fwd, twf)) ||
@@ -297,14 +295,6 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
       (rc = upload(&pl->d_status, std::vector<uint32_t>(1, 0u)))) {
     free_plan(pl);
     return rc;
-  }
-  if (pl->ws_words) {
-    cudaError_t e = cudaMalloc((void **)&pl->d_ws, pl->ws_words * sizeof(uint32_t));
-    if (e != cudaSuccess) {
-      pd_set_error("cudaMalloc(workspace)", e);
-      free_plan(pl);
-      return POLYDET_ENOMEM;
-    }
   }
   *out = pl;
   return POLYDET_OK;
@@ -331,7 +321,8 @@ extern "C" int polydet_plan_query(polydet_plan_t pl, polydet_plan_info *info) {
     info->D[v] = pl->D[v];
     info->N[v] = pl->N[v];
   }
-  info->workspace_bytes = pl->ws_words * sizeof(uint32_t);
+  info->eval_ws_words = pl->eval_ws_words;
+  info->interp_ws_words = pl->interp_ws_words;
   return POLYDET_OK;
 }
 

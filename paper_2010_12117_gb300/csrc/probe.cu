@@ -1,0 +1,85 @@
+// Measurement utility: the integer-pipe ceilings that bound condensation.
+//
+// Two in-register streams with eight independent dependency chains per
+// thread, enough warps per SM to hide latency, and no memory traffic:
+//  - plain 32-bit multiply-adds (x = x * x + c), the IMAD rate;
+//  - the condensation update r = (a*b - c*d) / R mod p (two 32x32->64
+//    multiply-adds, one REDC), the fused-update rate.
+// The rates bound the determinant kernels the way a copy bounds a memory
+// kernel.
+#include "common.cuh"
+
+__global__ void __launch_bounds__(256) imad_probe(uint32_t *out, int iters, uint32_t seed) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = seed + tid * 8u + j;
+  // x <- x * x + j: a quadratic map, so no two iterations fold into one
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = x[j] * x[j] + (uint32_t)j;
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s ^= x[j];
+  if (s == 0x12345678u) out[tid] = s;  // practically never taken; keeps the chains live
+}
+
+__global__ void __launch_bounds__(256) update_probe(uint32_t *out, int iters, uint32_t p,
+                                                    uint32_t pinv, uint32_t seed) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t a[8], f[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    a[j] = (seed + tid * 8u + j) % p;
+    f[j] = (seed * 3u + j * 7919u) % p;
+  }
+  const uint32_t piv = (seed ^ 0x5bd1e995u) % p, c = (seed + 12345u) % p;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = mfms(piv, a[j], f[j], c, p, pinv);
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s ^= a[j];
+  if (s == 0x12345678u) out[tid] = s;
+}
+
+extern "C" int polydet_probe_int_peaks(void *stream, double *imad_per_s, double *update_per_s) {
+  if (!imad_per_s || !update_per_s) return POLYDET_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  PD_CUDA(cudaGetDevice(&dev));
+  PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 256, blocks = sms * 8;
+  uint32_t *out = nullptr;  // never written in practice; a valid target all the same
+  PD_CUDA(cudaMallocAsync((void **)&out, (size_t)blocks * threads * sizeof(uint32_t), st));
+  cudaEvent_t e0, e1;
+  PD_CUDA(cudaEventCreate(&e0));
+  PD_CUDA(cudaEventCreate(&e1));
+  const uint32_t p = 2130706433u;
+  uint32_t pinv = 1;
+  for (int i = 0; i < 5; ++i) pinv *= 2u - p * pinv;
+  const int iters = 4096;
+  float ms = 0;
+  // warm-up, then timed
+  imad_probe<<<blocks, threads, 0, st>>>(out, iters, 1u);
+  PD_CUDA(cudaEventRecord(e0, st));
+  imad_probe<<<blocks, threads, 0, st>>>(out, iters, 2u);
+  PD_CUDA(cudaEventRecord(e1, st));
+  PD_CUDA(cudaEventSynchronize(e1));
+  PD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  *imad_per_s = (double)blocks * threads * iters * 8.0 / (ms * 1e-3);
+  update_probe<<<blocks, threads, 0, st>>>(out, iters / 4, p, pinv, 1u);
+  PD_CUDA(cudaEventRecord(e0, st));
+  update_probe<<<blocks, threads, 0, st>>>(out, iters / 4, p, pinv, 2u);
+  PD_CUDA(cudaEventRecord(e1, st));
+  PD_CUDA(cudaEventSynchronize(e1));
+  PD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  *update_per_s = (double)blocks * threads * (iters / 4) * 8.0 / (ms * 1e-3);
+  PD_CUDA(cudaFreeAsync(out, st));
+  PD_CUDA(cudaStreamSynchronize(st));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return POLYDET_OK;
+}

@@ -37,7 +37,7 @@ def prime_count(coeffs: np.ndarray) -> int:
 
 
 def _chunk(plan: Plan, budget_bytes: int) -> int:
-    per_prime = 4 * (plan.n * plan.n * plan.G + plan.G)
+    per_prime = 4 * (plan.n * plan.n * plan.G + plan.G + max(plan.eval_ws_words, plan.interp_ws_words))
     return max(1, min(plan.P, budget_bytes // max(1, per_prime)))
 
 
@@ -70,6 +70,7 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
         ch = _chunk(plan, budget_bytes)
         evals = torch.empty(ch * n * n * plan.G, dtype=torch.int32, device=dev) if todo else None
         detv = torch.empty(ch * plan.G, dtype=torch.int32, device=dev) if todo else None
+        ws = plan.workspace(ch) if todo else None
         runs: List[List[int]] = []  # consecutive primes, at most ch per launch
         for q in todo:
             if runs and runs[-1][1] == q and runs[-1][1] - runs[-1][0] < ch:
@@ -79,9 +80,9 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
         for done, (lo, hi) in enumerate(runs):
             if stop_after_chunks is not None and done >= stop_after_chunks:
                 raise InterruptedError("stopped after the requested number of chunks")
-            plan.eval(c_dev, lo, hi, evals, st)
+            plan.eval(c_dev, lo, hi, evals, ws, st)
             plan.condense(evals, lo, hi, detv, st)
-            plan.interp(detv, lo, hi, residues[lo * plan.C:hi * plan.C], st)
+            plan.interp(detv, lo, hi, residues[lo * plan.C:hi * plan.C], ws, st)
             if store is not None:
                 host = as_u32(residues[lo * plan.C:hi * plan.C])
                 for q in range(lo, hi):

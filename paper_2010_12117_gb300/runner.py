@@ -1,0 +1,158 @@
+"""Prepared determinant jobs: plans, device buffers and pinned host staging
+for a fixed list of polynomial matrices, computed by the plain path
+(Algorithm 1 per matrix: eval -> condense -> interp per prime chunk, then
+CRT), all asynchronous on one stream.
+
+``upload`` copies the inputs from pinned host memory, ``compute`` runs every
+stage on the device, ``download`` copies the limbs back; ``results`` turns
+them into Python integers.  ``StageTimer`` brackets each library call with
+CUDA events on the launching stream so per-kernel time can be attributed.
+"""
+from __future__ import annotations
+
+from collections import defaultdict
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from .binding import EBOUND, Plan, PolydetError, as_u32, limbs_to_ints
+from .pipeline import prime_count
+
+
+class StageTimer:
+    """Events around library calls, grouped by stage name, with the
+    algorithmic work each call represents."""
+
+    def __init__(self):
+        self.events: Dict[str, list] = defaultdict(list)
+        self.work: Dict[str, float] = defaultdict(float)
+        self.launches: Dict[str, int] = defaultdict(int)
+
+    def run(self, name: str, stream: torch.cuda.Stream, fn, work: float = 0.0, launches: int = 1):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        self.events[name].append((s, e))
+        self.work[name] += work
+        self.launches[name] += launches
+
+    def ms(self) -> Dict[str, float]:
+        return {k: sum(s.elapsed_time(e) for s, e in v) for k, v in self.events.items()}
+
+
+def condense_updates(n: int) -> int:
+    """Fused modular updates of one n x n elimination: sum_c (n-1-c)^2."""
+    return (n - 1) * n * (2 * n - 1) // 6
+
+
+class PlainRunner:
+    def __init__(self, mats: Sequence, nprimes: Optional[Sequence[int]] = None,
+                 budget_bytes: int = 6 << 30, device: str = "cuda"):
+        self.mats = list(mats)
+        self.plans: List[Plan] = []
+        for i, pm in enumerate(self.mats):
+            P = nprimes[i] if nprimes is not None else prime_count(pm.coeffs)
+            self.plans.append(Plan(pm.n, pm.degs, P))
+        self.dev = torch.device(device)
+        co, ro, lo = [0], [0], [0]
+        for pm, pl in zip(self.mats, self.plans):
+            co.append(co[-1] + pm.n * pm.n * pl.E)
+            ro.append(ro[-1] + pl.P * pl.C)
+            lo.append(lo[-1] + pl.C * pl.W)
+        self.coef_off, self.res_off, self.limb_off = co, ro, lo
+        # prime chunks per job under the scratch budget
+        self.chunks: List[List[tuple]] = []
+        max_ev = max_dv = max_ws = 1
+        for pm, pl in zip(self.mats, self.plans):
+            per = 4 * (pm.n * pm.n * pl.G + pl.G + max(pl.eval_ws_words, pl.interp_ws_words))
+            ch = max(1, min(pl.P, budget_bytes // per))
+            self.chunks.append([(a, min(pl.P, a + ch)) for a in range(0, pl.P, ch)])
+            max_ev = max(max_ev, ch * pm.n * pm.n * pl.G)
+            max_dv = max(max_dv, ch * pl.G)
+            max_ws = max(max_ws, ch * max(pl.eval_ws_words, pl.interp_ws_words))
+        self.coeffs_dev = torch.empty(co[-1], dtype=torch.int32, device=self.dev)
+        self.residues = torch.empty(max(ro[-1], 1), dtype=torch.int32, device=self.dev)
+        self.limbs = torch.empty(max(lo[-1], 1), dtype=torch.int32, device=self.dev)
+        self.evals = torch.empty(max_ev, dtype=torch.int32, device=self.dev)
+        self.detvals = torch.empty(max_dv, dtype=torch.int32, device=self.dev)
+        self.ws = torch.empty(max_ws, dtype=torch.int32, device=self.dev)
+        self.host_in = torch.empty(co[-1], dtype=torch.int32, pin_memory=True)
+        self.host_out = torch.empty(max(lo[-1], 1), dtype=torch.int32, pin_memory=True)
+        for i, pm in enumerate(self.mats):
+            self.host_in[co[i]:co[i + 1]] = torch.from_numpy(
+                np.ascontiguousarray(pm.coeffs, dtype=np.int32).reshape(-1))
+
+    # -- sizes ---------------------------------------------------------------
+    @property
+    def h2d_bytes(self) -> int:
+        return 4 * self.coef_off[-1]
+
+    @property
+    def d2h_bytes(self) -> int:
+        return 4 * self.limb_off[-1]
+
+    def modp_dets(self) -> int:
+        return sum(pl.P * pl.G for pl in self.plans)
+
+    def kernel_launches(self) -> int:
+        tot = 0
+        for pl, chunks in zip(self.plans, self.chunks):
+            tot += len(chunks) * (2 * pl.k + 1) + 1
+        return tot
+
+    # -- the three phases ----------------------------------------------------
+    def upload(self, stream: torch.cuda.Stream) -> None:
+        with torch.cuda.stream(stream):
+            self.coeffs_dev.copy_(self.host_in, non_blocking=True)
+
+    def compute(self, stream: torch.cuda.Stream, timer: Optional[StageTimer] = None) -> None:
+        for i, (pm, pl) in enumerate(zip(self.mats, self.plans)):
+            c = self.coeffs_dev[self.coef_off[i]:self.coef_off[i + 1]]
+            res = self.residues[self.res_off[i]:self.res_off[i + 1]]
+            n2 = pm.n * pm.n
+            for lo, hi in self.chunks[i]:
+                np_ = hi - lo
+                r = res[lo * pl.C:hi * pl.C]
+                calls = [
+                    ("eval", lambda: pl.eval(c, lo, hi, self.evals, self.ws, stream),
+                     4.0 * np_ * n2 * (pl.E + pl.G), pl.k),
+                    ("condense", lambda: pl.condense(self.evals, lo, hi, self.detvals, stream),
+                     float(np_ * pl.G * condense_updates(pm.n)), 1),
+                    ("interp", lambda: pl.interp(self.detvals, lo, hi, r, self.ws, stream),
+                     4.0 * np_ * (pl.G + pl.C), pl.k),
+                ]
+                for name, fn, work, nl in calls:
+                    if timer is None:
+                        fn()
+                    else:
+                        timer.run(name, stream, fn, work, nl)
+            lb = self.limbs[self.limb_off[i]:self.limb_off[i + 1]]
+            fn = lambda: pl.crt(res, lb, stream)  # noqa: E731
+            if timer is None:
+                fn()
+            else:
+                timer.run("crt", stream, fn, 4.0 * pl.C * (pl.P + pl.W), 1)
+
+    def download(self, stream: torch.cuda.Stream) -> None:
+        with torch.cuda.stream(stream):
+            self.host_out.copy_(self.limbs, non_blocking=True)
+
+    def check_status(self, stream: torch.cuda.Stream) -> None:
+        for pl in self.plans:
+            st = pl.sync_status(stream)
+            if st:
+                raise PolydetError(EBOUND, f"device status {st:#x}")
+
+    def results(self) -> List[List[int]]:
+        out = []
+        host = self.host_out.numpy().view(np.uint32)
+        for i, pl in enumerate(self.plans):
+            out.append(limbs_to_ints(host[self.limb_off[i]:self.limb_off[i + 1]].reshape(pl.C, pl.W), pl.W))
+        return out
+
+    def close(self) -> None:
+        for pl in self.plans:
+            pl.close()

@@ -56,7 +56,7 @@ def test_eval_matches_direct_evaluation(n, degs, P, sample):
     pl = Plan(n, degs, P)
     coeffs = torch.from_numpy(pm.coeffs.astype(np.int32).reshape(-1)).cuda()
     evals = torch.empty(P * n * n * pl.G, dtype=torch.int32, device="cuda")
-    pl.eval(coeffs, 0, P, evals)
+    pl.eval(coeffs, 0, P, evals, pl.workspace(P))
     torch.cuda.synchronize()
     got = u32(evals).reshape(P, n * n, pl.G)
     nodes = range(pl.G) if sample is None else sorted(set(
@@ -82,8 +82,8 @@ def test_eval_prime_range_offsets():
     coeffs = torch.from_numpy(pm.coeffs.astype(np.int32).reshape(-1)).cuda()
     full = torch.empty(4 * n * n * pl.G, dtype=torch.int32, device="cuda")
     part = torch.empty(2 * n * n * pl.G, dtype=torch.int32, device="cuda")
-    pl.eval(coeffs, 0, 4, full)
-    pl.eval(coeffs, 2, 4, part)
+    pl.eval(coeffs, 0, 4, full, pl.workspace(4))
+    pl.eval(coeffs, 2, 4, part, pl.workspace(2))
     torch.cuda.synchronize()
     assert np.array_equal(u32(full)[2 * n * n * pl.G:], u32(part))
 
@@ -165,7 +165,7 @@ def test_interp_round_trip_against_oracle():
         det_vals[q] = modular.eval_grid(vec, pl.D, pl.N, pl.roots[q], p)
     dv = torch.from_numpy(det_vals.astype(np.uint32).view(np.int32).reshape(-1)).cuda()
     res = torch.empty(P * pl.C, dtype=torch.int32, device="cuda")
-    pl.interp(dv, 0, P, res)
+    pl.interp(dv, 0, P, res, pl.workspace(P))
     assert pl.sync_status() == 0
     got = u32(res).reshape(P, pl.C)
     for q in range(P):
@@ -186,7 +186,7 @@ def test_interp_flags_a_degree_bound_violation():
     vals = rng.integers(0, pl.primes[0], pl.G, dtype=np.uint64).astype(np.uint32)
     dv = torch.from_numpy(vals.view(np.int32)).cuda()
     res = torch.empty(pl.C, dtype=torch.int32, device="cuda")
-    pl.interp(dv, 0, 1, res)
+    pl.interp(dv, 0, 1, res, pl.workspace(1))
     assert pl.sync_status() & 1
     assert pl.sync_status() == 0  # reading clears it
     # the kept coefficients still equal the oracle's inverse DFT of those values
@@ -222,13 +222,16 @@ def test_invalid_arguments_are_rejected():
     pl = Plan(4, (2, 2), 2)
     buf = torch.empty(16, dtype=torch.int32, device="cuda")
     with pytest.raises(ValueError):
-        pl.eval(buf, 0, 2, buf)  # too small
+        pl.eval(buf, 0, 2, buf, pl.workspace(2))  # too small
+    with pytest.raises(ValueError):
+        big0 = torch.empty(2 * 16 * pl.G, dtype=torch.int32, device="cuda")
+        pl.eval(torch.zeros(16 * 9, dtype=torch.int32, device="cuda"), 0, 2, big0)  # no workspace
     big = torch.empty(4 * 16 * pl.G, dtype=torch.int32, device="cuda")
     with pytest.raises(PolydetError) as ei:
         pl.condense(big, 1, 1, big)  # empty range
     assert ei.value.code == EINVAL
     with pytest.raises(PolydetError):
-        pl.interp(big, 0, 3, big)  # beyond P
+        pl.interp(big, 0, 3, big, pl.workspace(3))  # beyond P
     with pytest.raises(PolydetError):
         Plan(33, (1,), 2)
     with pytest.raises(PolydetError):
