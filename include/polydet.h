@@ -146,6 +146,82 @@ int polydet_crt(polydet_plan_t plan, const uint32_t *residues_dev, uint32_t *lim
  * it.  Returns POLYDET_EBOUND / POLYDET_ETIMEOUT if the matching bit was set. */
 int polydet_sync_status(polydet_plan_t plan, void *stream, uint32_t *status_out);
 
+/* ------------------------------------------------------------------------
+ * Batches: many jobs of uneven order, variable count, degree and prime
+ * count in one run (the data-parallel loop of Algorithm 1 over matrices,
+ * primes and nodes at once).  Evaluation of the last variable is fused into
+ * the determinant kernel, so evaluated matrices never reach memory: one
+ * persistent kernel per matrix order takes (job, prime, node-block) items
+ * from a counter kept in the caller's workspace.
+ *
+ * Buffers are caller-owned device arrays laid out by the batch; job j
+ * occupies words [off[j], off[j+1]) of each (polydet_batch_offsets):
+ *   coeffs   int32  : job j's [n][n][E] coefficients, as for polydet_eval
+ *   partial  uint32 : every variable but the last evaluated (eval -> condense)
+ *   detvals  uint32 : [P][G] determinants at the nodes (as condense_batch)
+ *   residues uint32 : [P][C] determinant residues (as polydet_interp)
+ *   limbs    uint32 : [C][W] signed coefficients (as polydet_crt)
+ *   workspace uint32: info.workspace_words words (counters + scratch).
+ * Constraint: the last variable's entry degree d_k is at most 7.
+ * A run is eval, condense, interp, crt on one stream; no call in a run
+ * allocates or synchronises, so a run can be captured in a CUDA graph.
+ * ------------------------------------------------------------------------ */
+typedef struct polydet_job {
+  int32_t n;                   /* matrix order, 1..32                     */
+  int32_t nvars;               /* variables, 1..POLYDET_MAX_VARS          */
+  int32_t nprimes;             /* primes (polydet_hadamard_primes)        */
+  int32_t d[POLYDET_MAX_VARS]; /* entry degree bound per variable         */
+} polydet_job;
+
+typedef struct polydet_batch_s *polydet_batch_t;
+
+typedef struct polydet_batch_info {
+  int32_t njobs;
+  int64_t coeff_words, partial_words, detval_words, residue_words, limb_words;
+  uint64_t workspace_words;
+  int64_t items[POLYDET_MAX_N + 1];   /* fused work items per matrix order  */
+  int32_t threads[POLYDET_MAX_N + 1]; /* CTA size per matrix order          */
+  int32_t blocks[POLYDET_MAX_N + 1];  /* persistent CTAs per matrix order   */
+} polydet_batch_info;
+
+#define POLYDET_OFF_COEFFS 0
+#define POLYDET_OFF_PARTIAL 1
+#define POLYDET_OFF_DETVALS 2
+#define POLYDET_OFF_RESIDUES 3
+#define POLYDET_OFF_LIMBS 4
+
+/* Plan a batch from host `jobs[njobs]` (one polydet_plan per job is built;
+ * small device tables only).  flags must be 0. */
+int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs, int njobs, uint32_t flags);
+int polydet_batch_destroy(polydet_batch_t batch);
+int polydet_batch_query(polydet_batch_t batch, polydet_batch_info *info);
+/* Host `out[njobs + 1]` word offsets of buffer `which` (POLYDET_OFF_*). */
+int polydet_batch_offsets(polydet_batch_t batch, int which, int64_t *out);
+/* The plan of job `job` (owned by the batch; do not destroy). */
+int polydet_batch_job_plan(polydet_batch_t batch, int job, polydet_plan_t *plan_out);
+/* CTA size (multiple of 32 and of the lanes per determinant, <= 128) of the
+ * fused kernel for matrix order n; the autotuner's knob.  Not during a
+ * graph capture (uploads the segment table). */
+int polydet_batch_set_launch(polydet_batch_t batch, int n, int threads);
+
+/* Stage 1 of a batch: every variable but the last (Sec. 3.1). */
+int polydet_batch_eval(polydet_batch_t batch, const int32_t *coeffs_dev, uint32_t *partial_dev,
+                       uint32_t *ws_dev, void *stream);
+/* Stage 2: last-variable evaluation fused with condensation (Sec. 3.1-3.2),
+ * all orders (n = 0 in polydet_batch_condense_n) or only order n. */
+int polydet_batch_condense(polydet_batch_t batch, const uint32_t *partial_dev,
+                           uint32_t *detvals_dev, uint32_t *ws_dev, void *stream);
+int polydet_batch_condense_n(polydet_batch_t batch, int n, const uint32_t *partial_dev,
+                             uint32_t *detvals_dev, uint32_t *ws_dev, void *stream);
+/* Stage 3: interpolation per job (Sec. 3.3). */
+int polydet_batch_interp(polydet_batch_t batch, const uint32_t *detvals_dev,
+                         uint32_t *residues_dev, uint32_t *ws_dev, void *stream);
+/* Stage 4: Garner CRT per job (Sec. 3.4). */
+int polydet_batch_crt(polydet_batch_t batch, const uint32_t *residues_dev, uint32_t *limbs_dev,
+                      void *stream);
+/* OR of every job's status word (synchronises; clears them). */
+int polydet_batch_sync_status(polydet_batch_t batch, void *stream, uint32_t *status_out);
+
 /* Measurement utility (not a stage of the method): runs two in-register
  * integer streams on every SM and reports their rates, the ceilings of the
  * condensation kernels - plain 32-bit multiply-adds per second, and fused

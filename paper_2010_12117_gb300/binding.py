@@ -38,6 +38,23 @@ class PlanInfo(ctypes.Structure):
                 ("eval_ws_words", ctypes.c_uint64), ("interp_ws_words", ctypes.c_uint64)]
 
 
+MAX_N = 32
+OFF_COEFFS, OFF_PARTIAL, OFF_DETVALS, OFF_RESIDUES, OFF_LIMBS = 0, 1, 2, 3, 4
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nvars", ctypes.c_int32), ("nprimes", ctypes.c_int32),
+                ("d", ctypes.c_int32 * MAX_VARS)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("njobs", ctypes.c_int32), ("coeff_words", ctypes.c_int64),
+                ("partial_words", ctypes.c_int64), ("detval_words", ctypes.c_int64),
+                ("residue_words", ctypes.c_int64), ("limb_words", ctypes.c_int64),
+                ("workspace_words", ctypes.c_uint64), ("items", ctypes.c_int64 * (MAX_N + 1)),
+                ("threads", ctypes.c_int32 * (MAX_N + 1)), ("blocks", ctypes.c_int32 * (MAX_N + 1))]
+
+
 _lib = None
 
 # name -> (restype, argtypes); the exported C ABI.
@@ -59,6 +76,18 @@ SIGNATURES = {
     "polydet_interp": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP]),
     "polydet_crt": (_I, [_VP, _VP, _VP, _VP]),
     "polydet_sync_status": (_I, [_VP, _VP, _PU32]),
+    "polydet_batch_plan": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(Job), _I, _U32]),
+    "polydet_batch_destroy": (_I, [_VP]),
+    "polydet_batch_query": (_I, [_VP, ctypes.POINTER(BatchInfo)]),
+    "polydet_batch_offsets": (_I, [_VP, _I, _PI64]),
+    "polydet_batch_job_plan": (_I, [_VP, _I, ctypes.POINTER(_VP)]),
+    "polydet_batch_set_launch": (_I, [_VP, _I, _I]),
+    "polydet_batch_eval": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "polydet_batch_condense": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "polydet_batch_condense_n": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
+    "polydet_batch_interp": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "polydet_batch_crt": (_I, [_VP, _VP, _VP, _VP]),
+    "polydet_batch_sync_status": (_I, [_VP, _VP, _PU32]),
     "polydet_probe_int_peaks": (_I, [_VP, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]),
     "polydet_last_error": (ctypes.c_char_p, []),
@@ -217,6 +246,91 @@ class Plan:
         rc = lib().polydet_sync_status(self._h, _stream(stream), ctypes.byref(st))
         if rc not in (OK, EBOUND, ETIMEOUT):
             _check(rc, "polydet_sync_status")
+        return st.value
+
+
+class Batch:
+    """A polydet batch: jobs of any shape, one fused run for all of them.
+    ``jobs`` is a list of (n, degs, nprimes)."""
+
+    def __init__(self, jobs: Sequence[tuple]):
+        L = lib()
+        arr = (Job * len(jobs))()
+        for i, (n, degs, P) in enumerate(jobs):
+            arr[i].n, arr[i].nvars, arr[i].nprimes = int(n), len(degs), int(P)
+            for v, dv in enumerate(degs):
+                arr[i].d[v] = int(dv)
+        h = ctypes.c_void_p()
+        _check(L.polydet_batch_plan(ctypes.byref(h), arr, len(jobs), 0), "polydet_batch_plan")
+        self._h = h
+        self.njobs = len(jobs)
+        self.refresh()
+        self.offsets = {}
+        for name, which in (("coeffs", OFF_COEFFS), ("partial", OFF_PARTIAL), ("detvals", OFF_DETVALS),
+                            ("residues", OFF_RESIDUES), ("limbs", OFF_LIMBS)):
+            out = (ctypes.c_int64 * (self.njobs + 1))()
+            _check(L.polydet_batch_offsets(h, which, out), "polydet_batch_offsets")
+            self.offsets[name] = list(out)
+        self.job_info = []
+        for j in range(self.njobs):
+            ph = ctypes.c_void_p()
+            _check(L.polydet_batch_job_plan(h, j, ctypes.byref(ph)), "polydet_batch_job_plan")
+            info = PlanInfo()
+            _check(L.polydet_plan_query(ph, ctypes.byref(info)), "polydet_plan_query")
+            self.job_info.append(info)
+
+    def refresh(self) -> None:
+        info = BatchInfo()
+        _check(lib().polydet_batch_query(self._h, ctypes.byref(info)), "polydet_batch_query")
+        self.info = info
+        self.words = {"coeffs": info.coeff_words, "partial": info.partial_words,
+                      "detvals": info.detval_words, "residues": info.residue_words,
+                      "limbs": info.limb_words, "workspace": int(info.workspace_words)}
+
+    def orders(self) -> List[int]:
+        return [n for n in range(1, MAX_N + 1) if self.info.items[n] > 0]
+
+    def set_launch(self, n: int, threads: int) -> None:
+        _check(lib().polydet_batch_set_launch(self._h, int(n), int(threads)), "polydet_batch_set_launch")
+        self.refresh()
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().polydet_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _p(self, t, name):
+        return _ptr(t, torch.int32, max(1, self.words[name]), name)
+
+    def eval(self, coeffs, partial, ws, stream=None):
+        _check(lib().polydet_batch_eval(self._h, self._p(coeffs, "coeffs"), self._p(partial, "partial"),
+                                        self._p(ws, "workspace"), _stream(stream)), "polydet_batch_eval")
+
+    def condense(self, partial, detvals, ws, stream=None, n: int = 0):
+        _check(lib().polydet_batch_condense_n(self._h, int(n), self._p(partial, "partial"),
+                                              self._p(detvals, "detvals"), self._p(ws, "workspace"),
+                                              _stream(stream)), "polydet_batch_condense")
+
+    def interp(self, detvals, residues, ws, stream=None):
+        _check(lib().polydet_batch_interp(self._h, self._p(detvals, "detvals"),
+                                          self._p(residues, "residues"), self._p(ws, "workspace"),
+                                          _stream(stream)), "polydet_batch_interp")
+
+    def crt(self, residues, limbs, stream=None):
+        _check(lib().polydet_batch_crt(self._h, self._p(residues, "residues"), self._p(limbs, "limbs"),
+                                       _stream(stream)), "polydet_batch_crt")
+
+    def sync_status(self, stream=None) -> int:
+        st = ctypes.c_uint32(0)
+        rc = lib().polydet_batch_sync_status(self._h, _stream(stream), ctypes.byref(st))
+        if rc not in (OK, EBOUND, ETIMEOUT):
+            _check(rc, "polydet_batch_sync_status")
         return st.value
 
 

@@ -20,8 +20,11 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libpolydet.so")
 
-SOURCES = ["plan.cu", "ntt.cu", "crt.cu", "probe.cu", "condense_a.cu", "condense_b.cu",
-           "condense_c.cu", "condense_d.cu"]
+SOURCES = ["plan.cu", "ntt.cu", "crt.cu", "probe.cu", "batch.cu", "dispatch.cu"]
+# condense_inst.cu and fused_inst.cu are compiled once per range of matrix
+# orders (must match the ranges in csrc/dispatch.cu)
+KERNEL_RANGES = [(1, 6), (7, 10), (11, 12), (13, 16), (17, 20), (21, 24), (25, 28), (29, 32)]
+TEMPLATED = ["condense_inst.cu", "fused_inst.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
@@ -46,8 +49,8 @@ def _stale(obj: str, src: str, headers) -> bool:
     return any(os.path.getmtime(x) > t for x in [src, *headers])
 
 
-def _compile(src: str, obj: str, verbose_ptxas: bool) -> None:
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, obj: str, verbose_ptxas: bool, defs=()) -> None:
+    cmd = [nvcc(), *ARCH, *FLAGS, *defs, "-c", src, "-o", obj]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -63,15 +66,21 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     headers = _headers()
     todo = []
     objs = []
-    for s in SOURCES:
+    units = [(s, s.replace(".cu", ".o"), []) for s in SOURCES]
+    for s in TEMPLATED:
+        for lo, hi in KERNEL_RANGES:
+            units.append((s, s.replace(".cu", f"_{lo}_{hi}.o"), [f"-DPD_N_LO={lo}", f"-DPD_N_HI={hi}"]))
+    for s, o, defs in units:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, o)
         objs.append(obj)
         if force or verbose_ptxas or _stale(obj, src, headers):
-            todo.append((src, obj))
+            todo.append((src, obj, defs))
+    # the templated kernel objects dominate the build: start them first
+    todo.sort(key=lambda t: 0 if t[2] else 1)
     if todo:
         with ThreadPoolExecutor(max_workers=jobs or min(len(todo), os.cpu_count() or 4)) as ex:
-            list(ex.map(lambda so: _compile(so[0], so[1], verbose_ptxas), todo))
+            list(ex.map(lambda u: _compile(u[0], u[1], verbose_ptxas, u[2]), todo))
     if todo or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]

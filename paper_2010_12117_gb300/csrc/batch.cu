@@ -1,0 +1,308 @@
+// Batches of determinant jobs of uneven shape (order, variables, degrees,
+// prime count): one plan per job, a shared layout of every buffer, and the
+// per-order segment tables of the fused kernels.
+//
+// A run is four calls on one stream (the whole run can be captured in a CUDA
+// graph; nothing in it allocates or synchronises):
+//   polydet_batch_eval      every variable but the last, per job (NTT passes)
+//   polydet_batch_condense  one persistent fused kernel per matrix order
+//   polydet_batch_interp    inverse NTT per job
+//   polydet_batch_crt       Garner CRT per job
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+constexpr int kCounterWords = 2 * (POLYDET_MAX_N + 1);  // one 64-bit counter per order
+constexpr uint64_t kWsHead = 256;                       // words reserved for the counters
+
+int pow2_at_least(int x) {
+  int v = 1;
+  while (v < x) v <<= 1;
+  return v;
+}
+}  // namespace
+
+struct polydet_batch_s {
+  int njobs = 0;
+  std::vector<polydet_plan_t> plans;
+  std::vector<int> Lp;
+  std::vector<int64_t> coeff_off, part_off, det_off, res_off, limb_off;  // [njobs + 1]
+  uint64_t ws_words = 0;
+  int sms = 0;
+  int threads[POLYDET_MAX_N + 1] = {};
+  int blocks[POLYDET_MAX_N + 1] = {};
+  int64_t nitems[POLYDET_MAX_N + 1] = {};
+  size_t qwords[POLYDET_MAX_N + 1] = {};
+  std::vector<FusedSeg> segs[POLYDET_MAX_N + 1];
+  FusedSeg *d_segs[POLYDET_MAX_N + 1] = {};
+};
+
+static void destroy_batch(polydet_batch_s *b) {
+  if (!b) return;
+  for (auto p : b->plans) polydet_plan_destroy(p);
+  for (int n = 0; n <= POLYDET_MAX_N; ++n) cudaFree(b->d_segs[n]);
+  delete b;
+}
+
+// (Re)number the items of order n for the current CTA size and upload.
+static int build_class(polydet_batch_s *b, int n) {
+  auto &v = b->segs[n];
+  if (v.empty()) return POLYDET_OK;
+  const int S = b->threads[n] / pd_fused_team(n);
+  int64_t it = 0;
+  for (auto &s : v) {
+    s.item0 = it;
+    it += (s.G + S - 1) / S;
+  }
+  b->nitems[n] = it;
+  // shared memory for the partial-tensor rows of one item: S / N_k rows (items
+  // are S-aligned and S, N_k are powers of two) or one
+  size_t qw = 0;
+  for (const auto &s : v) {
+    const int64_t Nk = (int64_t)1 << s.logNk;
+    const int64_t rows = S > Nk ? S / Nk : 1;
+    qw = std::max<size_t>(qw, (size_t)rows * n * n * s.Lp);
+  }
+  b->qwords[n] = qw;
+  int bps = 0;
+  int rc = pd_fused_occupancy(n, b->threads[n], qw, &bps);
+  if (rc) return rc;
+  if (bps < 1) return POLYDET_EINVAL;  // the CTA's shared memory does not fit
+  b->blocks[n] = (int)std::min<int64_t>(it, (int64_t)bps * b->sms);
+  if (!b->d_segs[n]) PD_CUDA(cudaMalloc((void **)&b->d_segs[n], v.size() * sizeof(FusedSeg)));
+  PD_CUDA(cudaMemcpy(b->d_segs[n], v.data(), v.size() * sizeof(FusedSeg), cudaMemcpyHostToDevice));
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs, int njobs,
+                                  uint32_t flags) {
+  if (!out || !jobs || njobs < 1 || flags != 0) return POLYDET_EINVAL;
+  polydet_batch_s *b = new polydet_batch_s();
+  b->njobs = njobs;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete b;
+    return POLYDET_ECUDA;
+  }
+  b->coeff_off.assign(1, 0);
+  b->part_off.assign(1, 0);
+  b->det_off.assign(1, 0);
+  b->res_off.assign(1, 0);
+  b->limb_off.assign(1, 0);
+  uint64_t ws = 0;
+  for (int j = 0; j < njobs; ++j) {
+    const polydet_job &jb = jobs[j];
+    if (jb.nvars < 1 || jb.nvars > POLYDET_MAX_VARS || jb.d[jb.nvars - 1] + 1 > 8) {
+      destroy_batch(b);
+      return POLYDET_EINVAL;
+    }
+    polydet_plan_t pl = nullptr;
+    int rc = polydet_plan(&pl, jb.n, jb.nvars, jb.d, jb.nprimes, 0);
+    if (rc) {
+      destroy_batch(b);
+      return rc;
+    }
+    b->plans.push_back(pl);
+    const int k = pl->nvars;
+    const int L = pl->d[k - 1] + 1;
+    const int Lp = pow2_at_least(L);
+    b->Lp.push_back(Lp);
+    const int64_t n2 = (int64_t)pl->n * pl->n;
+    const int64_t rows = pl->G / pl->N[k - 1];
+    const int64_t part = ((int64_t)pl->P * rows * n2 * Lp + 7) / 8 * 8;
+    b->coeff_off.push_back(b->coeff_off.back() + n2 * pl->E);
+    b->part_off.push_back(b->part_off.back() + part);
+    b->det_off.push_back(b->det_off.back() + (int64_t)pl->P * pl->G);
+    b->res_off.push_back(b->res_off.back() + (int64_t)pl->P * pl->C);
+    b->limb_off.push_back(b->limb_off.back() + pl->C * pl->W);
+    uint64_t need = std::max<uint64_t>(k > 1 ? pd_partial_ws_words(pl) : 0, pl->interp_ws_words) *
+                    (uint64_t)pl->P;
+    ws = std::max(ws, need);
+  }
+  b->ws_words = kWsHead + ws;
+  for (int j = 0; j < njobs; ++j) {
+    polydet_plan_s *pl = b->plans[j];
+    const int k = pl->nvars;
+    const int64_t n2 = (int64_t)pl->n * pl->n;
+    const int64_t rows = pl->G / pl->N[k - 1];
+    for (int q = 0; q < pl->P; ++q) {
+      FusedSeg s = {};
+      s.G = pl->G;
+      s.q_off = b->part_off[j] + (int64_t)q * rows * n2 * b->Lp[j];
+      s.det_off = b->det_off[j] + (int64_t)q * pl->G;
+      s.tw = pl->d_tw_fwd + (size_t)q * pl->tw_len + pl->tw_off[k - 1];
+      s.md = pl->mod_h[q];
+      s.rn = pl->rn_h[q];
+      s.logNk = pl->logN[k - 1];
+      s.L = pl->d[k - 1] + 1;
+      s.Lp = b->Lp[j];
+      b->segs[pl->n].push_back(s);
+    }
+  }
+  for (int n = 1; n <= POLYDET_MAX_N; ++n) {
+    b->threads[n] = 128;
+    int rc = build_class(b, n);
+    if (rc) {
+      destroy_batch(b);
+      return rc;
+    }
+  }
+  *out = b;
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_destroy(polydet_batch_t b) {
+  if (!b) return POLYDET_EINVAL;
+  destroy_batch(b);
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_query(polydet_batch_t b, polydet_batch_info *info) {
+  if (!b || !info) return POLYDET_EINVAL;
+  memset(info, 0, sizeof *info);
+  info->njobs = b->njobs;
+  info->coeff_words = b->coeff_off.back();
+  info->partial_words = b->part_off.back();
+  info->detval_words = b->det_off.back();
+  info->residue_words = b->res_off.back();
+  info->limb_words = b->limb_off.back();
+  info->workspace_words = b->ws_words;
+  for (int n = 1; n <= POLYDET_MAX_N; ++n) {
+    info->items[n] = b->nitems[n];
+    info->threads[n] = b->threads[n];
+    info->blocks[n] = b->blocks[n];
+  }
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_offsets(polydet_batch_t b, int which, int64_t *out) {
+  if (!b || !out) return POLYDET_EINVAL;
+  const std::vector<int64_t> *v = nullptr;
+  switch (which) {
+    case POLYDET_OFF_COEFFS: v = &b->coeff_off; break;
+    case POLYDET_OFF_PARTIAL: v = &b->part_off; break;
+    case POLYDET_OFF_DETVALS: v = &b->det_off; break;
+    case POLYDET_OFF_RESIDUES: v = &b->res_off; break;
+    case POLYDET_OFF_LIMBS: v = &b->limb_off; break;
+    default: return POLYDET_EINVAL;
+  }
+  memcpy(out, v->data(), v->size() * sizeof(int64_t));
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_job_plan(polydet_batch_t b, int job, polydet_plan_t *plan_out) {
+  if (!b || !plan_out || job < 0 || job >= b->njobs) return POLYDET_EINVAL;
+  *plan_out = b->plans[job];
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_set_launch(polydet_batch_t b, int n, int threads) {
+  if (!b || n < 1 || n > POLYDET_MAX_N) return POLYDET_EINVAL;
+  const int T = pd_fused_team(n);
+  if (threads < 32 || threads > 128 || threads % 32 || threads % T) return POLYDET_EINVAL;
+  b->threads[n] = threads;
+  return build_class(b, n);
+}
+
+// One-variable jobs: the partial tensor is the coefficients mod p_q,
+// out[q][entry][Lp] (l < L written).
+__global__ void repack_kernel(const int32_t *__restrict__ coeffs, uint32_t *__restrict__ out,
+                              int64_t n2, int L, int Lp, const ModP *__restrict__ mod) {
+  const int q = blockIdx.y;
+  const uint32_t p = mod[q].p;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n2 * L;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = f / L;
+    const int l = (int)(f - e * L);
+    out[(int64_t)q * n2 * Lp + e * Lp + l] = reduce_i32(coeffs[f], p);
+  }
+}
+
+extern "C" int polydet_batch_eval(polydet_batch_t b, const int32_t *coeffs, uint32_t *partial,
+                                  uint32_t *ws, void *stream) {
+  if (!b || !coeffs || !partial || !ws) return POLYDET_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int j = 0; j < b->njobs; ++j) {
+    polydet_plan_s *pl = b->plans[j];
+    if (pl->nvars == 1) {
+      const int64_t n2 = (int64_t)pl->n * pl->n;
+      const int L = pl->d[0] + 1;
+      const unsigned blocks = (unsigned)std::min<int64_t>((n2 * L + 255) / 256, 1024);
+      repack_kernel<<<dim3(blocks, pl->P), 256, 0, st>>>(coeffs + b->coeff_off[j],
+                                                         partial + b->part_off[j], n2, L, b->Lp[j],
+                                                         pl->d_mod);
+      PD_CUDA(cudaGetLastError());
+      continue;
+    }
+    int rc = pd_eval_partial(pl, coeffs + b->coeff_off[j], 0, pl->P, partial + b->part_off[j],
+                             b->Lp[j], ws + kWsHead, st);
+    if (rc) return rc;
+  }
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_condense_n(polydet_batch_t b, int n, const uint32_t *partial,
+                                        uint32_t *detvals, uint32_t *ws, void *stream) {
+  if (!b || !partial || !detvals || !ws || n < 0 || n > POLYDET_MAX_N) return POLYDET_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long *counters = reinterpret_cast<unsigned long long *>(ws);
+  if (n == 0) {
+    PD_CUDA(cudaMemsetAsync(counters, 0, kCounterWords * sizeof(uint32_t), st));
+  } else {
+    PD_CUDA(cudaMemsetAsync(counters + n, 0, sizeof(unsigned long long), st));
+  }
+  for (int m = 1; m <= POLYDET_MAX_N; ++m) {
+    if ((n && m != n) || b->segs[m].empty()) continue;
+    int rc = pd_fused_launch(m, b->d_segs[m], (int)b->segs[m].size(), b->nitems[m], partial,
+                             detvals, counters + m, b->threads[m], b->blocks[m], b->qwords[m], st);
+    if (rc) return rc;
+  }
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_condense(polydet_batch_t b, const uint32_t *partial, uint32_t *detvals,
+                                      uint32_t *ws, void *stream) {
+  return polydet_batch_condense_n(b, 0, partial, detvals, ws, stream);
+}
+
+extern "C" int polydet_batch_interp(polydet_batch_t b, const uint32_t *detvals, uint32_t *residues,
+                                    uint32_t *ws, void *stream) {
+  if (!b || !detvals || !residues || !ws) return POLYDET_EINVAL;
+  for (int j = 0; j < b->njobs; ++j) {
+    polydet_plan_s *pl = b->plans[j];
+    int rc = polydet_interp(pl, detvals + b->det_off[j], 0, pl->P, residues + b->res_off[j],
+                            ws + kWsHead, stream);
+    if (rc) return rc;
+  }
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_crt(polydet_batch_t b, const uint32_t *residues, uint32_t *limbs,
+                                 void *stream) {
+  if (!b || !residues || !limbs) return POLYDET_EINVAL;
+  for (int j = 0; j < b->njobs; ++j) {
+    int rc = polydet_crt(b->plans[j], residues + b->res_off[j], limbs + b->limb_off[j], stream);
+    if (rc) return rc;
+  }
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_sync_status(polydet_batch_t b, void *stream, uint32_t *status_out) {
+  if (!b) return POLYDET_EINVAL;
+  uint32_t all = 0;
+  int worst = POLYDET_OK;
+  for (auto pl : b->plans) {
+    uint32_t s = 0;
+    int rc = polydet_sync_status(pl, stream, &s);
+    all |= s;
+    if (rc == POLYDET_ECUDA) return rc;
+    if (rc && !worst) worst = rc;
+  }
+  if (status_out) *status_out = all;
+  return worst;
+}

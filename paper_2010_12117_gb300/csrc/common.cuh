@@ -105,6 +105,8 @@ struct polydet_plan_s {
   int tw_len;                      // sum_v N_v / 2: twiddles per prime
   uint32_t primes[POLYDET_MAX_PRIMES];
   uint32_t roots[POLYDET_MAX_PRIMES][POLYDET_MAX_VARS];
+  ModP mod_h[POLYDET_MAX_PRIMES];   // host copies of the per-prime constants
+  uint32_t rn_h[POLYDET_MAX_PRIMES];
 
   // device tables
   ModP *d_mod;            // [P]
@@ -135,3 +137,32 @@ void pd_set_error(const char *what, cudaError_t e);
 // Launchers implemented in separate translation units.
 int pd_launch_condense(const polydet_plan_s *pl, const uint32_t *evals, int prime_lo,
                        int nprimes, uint32_t *detvals, cudaStream_t st);
+
+// Evaluation of every variable but the last (x_k), for the fused kernels:
+// out[q][row][entry][Lp] with row over prod_{v<k} N_v (lex) holding the
+// coefficients of x_k^l, l < L = d_k + 1 (Lp >= L, padding unwritten).
+// Needs pd_partial_ws_words(pl) * (hi - lo) words of scratch.
+int pd_eval_partial(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int hi,
+                    uint32_t *out, int Lp, uint32_t *ws, cudaStream_t st);
+uint64_t pd_partial_ws_words(const polydet_plan_s *pl);
+
+// One (job, prime) pair of a fused launch: the nodes [0, G) of that job and
+// prime, cut into items of S consecutive nodes (S = threads / lanes per det).
+struct FusedSeg {
+  int64_t item0;       // index of the segment's first item
+  int64_t G;           // grid nodes
+  int64_t q_off;       // words into the partial tensor (or the int32 coefficients)
+  int64_t det_off;     // words into the determinant values
+  const uint32_t *tw;  // w_k^j * R for j < N_k / 2 (last variable, this prime)
+  ModP md;
+  uint32_t rn;         // R^n mod p
+  int32_t logNk;       // log2 N_k
+  int32_t L, Lp;       // coefficients of x_k per entry, stride of the partial tensor
+};
+
+int pd_fused_launch(int n, const FusedSeg *segs, int nsegs, int64_t nitems, const uint32_t *partial,
+                    uint32_t *detvals, unsigned long long *counter, int threads, int blocks,
+                    size_t qwords, cudaStream_t st);
+// qwords: words of partial-tensor rows one CTA stages (rows per item x n^2 x Lp)
+int pd_fused_occupancy(int n, int threads, size_t qwords, int *blocks_per_sm);
+int pd_fused_team(int n);

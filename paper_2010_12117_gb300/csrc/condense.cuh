@@ -123,18 +123,19 @@ struct TeamFor {
   static constexpr int value = NN <= 12 ? 1 : (NN <= 16 ? 2 : (NN <= 20 ? 4 : 8));
 };
 
-template <int NN>
-static int launch_condense_n(const polydet_plan_s *pl, const uint32_t *evals, int prime_lo,
+template <int NN, int HI>
+static int condense_dispatch(const polydet_plan_s *pl, const uint32_t *evals, int prime_lo,
                              int nprimes, uint32_t *detvals, cudaStream_t st) {
-  constexpr int T = TeamFor<NN>::value;
-  const int threads = 128;
-  const int64_t teams_per_cta = threads / T;
-  dim3 grid((unsigned)((pl->G + teams_per_cta - 1) / teams_per_cta), (unsigned)nprimes);
-  condense_kernel<NN, T><<<grid, threads, 0, st>>>(evals, detvals, pl->G, pl->d_mod, pl->d_rn, prime_lo);
-  PD_CUDA(cudaGetLastError());
-  return POLYDET_OK;
+  if (pl->n == NN) {
+    constexpr int T = TeamFor<NN>::value;
+    const int threads = 128;
+    const int64_t teams_per_cta = threads / T;
+    dim3 grid((unsigned)((pl->G + teams_per_cta - 1) / teams_per_cta), (unsigned)nprimes);
+    condense_kernel<NN, T><<<grid, threads, 0, st>>>(evals, detvals, pl->G, pl->d_mod, pl->d_rn,
+                                                     prime_lo);
+    PD_CUDA(cudaGetLastError());
+    return POLYDET_OK;
+  }
+  if constexpr (NN < HI) return condense_dispatch<NN + 1, HI>(pl, evals, prime_lo, nprimes, detvals, st);
+  return POLYDET_EINVAL;
 }
-
-#define PD_CONDENSE_CASE(NN) \
-  case NN:                   \
-    return launch_condense_n<NN>(pl, evals, prime_lo, nprimes, detvals, st);

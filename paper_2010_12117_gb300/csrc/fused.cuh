@@ -1,0 +1,239 @@
+// Fused evaluation + condensation for batches of matrices of any shape: the
+// last variable's evaluation (the last pass of Algorithm 2) is folded into
+// the determinant kernel (Algorithm 3), so the evaluated matrices are never
+// written to memory.
+//
+// Input per (job, prime): the partially evaluated tensor Q[row][entry][Lp],
+// every variable but x_k already evaluated (row = node of x_1..x_{k-1}), the
+// L = d_k + 1 coefficients of x_k left as they are.  One-variable jobs have
+// no pass before this one: their tensor is the coefficient array reduced mod
+// p (one row).
+//
+// The kernel is persistent: CTAs take items - S consecutive nodes of one
+// (job, prime) segment, S = threads / lanes per determinant - from a counter
+// in global memory until the list is exhausted, so one launch covers every
+// (job, prime) pair of a matrix order, whatever the mix of grid sizes.  Per
+// item:
+//  0. the CTA copies the Q rows its nodes need (S / N_k rows, or one) into
+//     shared memory with coalesced 16-byte loads;
+//  1. a team of T lanes owns node g = (row, i): it forms x = w_k^i
+//     (Montgomery form, from the twiddle table) and its powers, and evaluates
+//     each entry of its columns, sum_l Q[row][entry][l] x^l, with one REDC per
+//     two products (2 p^2 < p 2^32), into its own slice of shared memory
+//     (rolled loops: small code, no register pressure);
+//  2. the slice is loaded into the register-resident matrix and goes through
+//     the elimination of condense_kernel (Algorithm 3).
+#pragma once
+
+#include "condense.cuh"
+
+// Words of shared memory for the entry slices of a CTA of `threads` lanes.
+template <int NN>
+__host__ __device__ constexpr size_t fused_slice_words(int threads) {
+  return (size_t)((NN + TeamFor<NN>::value - 1) / TeamFor<NN>::value) * NN * threads;
+}
+
+template <int NN, int T>
+__device__ __forceinline__ void fused_eval_entries(const uint32_t *qrow, int t, const uint32_t (&X)[8],
+                                                   int L, int Lp, uint32_t p, uint32_t pinv,
+                                                   uint32_t *mine, int bd) {
+  constexpr int M = (NN + T - 1) / T;
+#pragma unroll 1
+  for (int m = 0; m < M; ++m) {
+    const int j = t + T * m;
+    if (j >= NN) break;
+#pragma unroll 2
+    for (int i = 0; i < NN; ++i) {
+      const uint32_t *q = qrow + (i * NN + j) * Lp;
+      uint32_t v[8];
+      if (Lp >= 4) {
+        const uint4 lo4 = *reinterpret_cast<const uint4 *>(q);
+        v[0] = lo4.x; v[1] = lo4.y; v[2] = lo4.z; v[3] = lo4.w;
+        if (Lp == 8) {
+          const uint4 hi4 = *(reinterpret_cast<const uint4 *>(q) + 1);
+          v[4] = hi4.x; v[5] = hi4.y; v[6] = hi4.z; v[7] = hi4.w;
+        } else {
+          v[4] = v[5] = v[6] = v[7] = 0u;
+        }
+      } else if (Lp == 2) {
+        const uint2 w2 = *reinterpret_cast<const uint2 *>(q);
+        v[0] = w2.x; v[1] = w2.y;
+        v[2] = v[3] = v[4] = v[5] = v[6] = v[7] = 0u;
+      } else {
+        v[0] = q[0];
+        v[1] = v[2] = v[3] = v[4] = v[5] = v[6] = v[7] = 0u;
+      }
+      uint32_t acc = v[0];
+      if (L > 1) {
+        uint64_t s = (uint64_t)v[1] * X[1];
+        if (L > 2) s += (uint64_t)v[2] * X[2];
+        acc = addm(acc, redc(s, p, pinv), p);
+      }
+      if (L > 3) {
+        uint64_t s = (uint64_t)v[3] * X[3];
+        if (L > 4) s += (uint64_t)v[4] * X[4];
+        acc = addm(acc, redc(s, p, pinv), p);
+      }
+      if (L > 5) {
+        uint64_t s = (uint64_t)v[5] * X[5];
+        if (L > 6) s += (uint64_t)v[6] * X[6];
+        acc = addm(acc, redc(s, p, pinv), p);
+      }
+      if (L > 7) acc = addm(acc, mmul(v[7], X[7], p, pinv), p);
+      mine[(m * NN + i) * bd] = acc;
+    }
+  }
+}
+
+// Node g's determinant (one team), from the entries in its slice.  Kept out
+// of line so that the register allocation of this straight-line body is not
+// constrained by the persistent loop around it.
+template <int NN, int T>
+__device__ __noinline__ void fused_det(const uint32_t *mine, int bd, int t, ModP md, uint32_t rn,
+                                       bool write, uint32_t *out) {
+  constexpr int M = (NN + T - 1) / T;
+  const uint32_t p = md.p, pinv = md.pinv;
+  uint32_t a[M][NN];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = t + T * m;
+#pragma unroll
+    for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? mine[(m * NN + i) * bd] : 0u;
+  }
+  uint32_t Q = md.r1, den = md.r1;
+  ElimStep<NN, T, 0>::run(a, t, p, pinv, Q, den);
+  const uint32_t inv = mpow(den, p - 2u, md.r1, p, pinv);
+  uint32_t res = mmul(Q, inv, p, pinv);
+  res = mmul(res, rn, p, pinv);
+  if (write) *out = res;
+}
+
+template <int NN, int T>
+__global__ void __launch_bounds__(128) fused_kernel(const FusedSeg *__restrict__ segs, int nsegs,
+                                                    long long nitems,
+                                                    const uint32_t *__restrict__ partial,
+                                                    uint32_t *__restrict__ detvals,
+                                                    unsigned long long *counter) {
+  constexpr int NN2 = NN * NN;
+  extern __shared__ uint4 fused_smem_u4[];
+  __shared__ long long s_item;
+  __shared__ int s_seg;
+  const int bd = blockDim.x;
+  uint32_t *ent = reinterpret_cast<uint32_t *>(fused_smem_u4);  // [M * NN][bd]
+  uint32_t *qsm = ent + fused_slice_words<NN>(bd);              // [rows][NN2][Lp]
+  const int t = (T == 1) ? 0 : (int)(threadIdx.x % T);
+  const int team = threadIdx.x / T;
+  const int S = bd / T;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(counter, 1ull);
+      int lo = 0;
+      if (it < nitems) {
+        int hi = nsegs - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (segs[mid].item0 <= it) lo = mid; else hi = mid - 1;
+        }
+      }
+      s_item = it;
+      s_seg = lo;
+    }
+    __syncthreads();
+    const long long item = s_item;
+    const int si = s_seg;
+    __syncthreads();
+    if (item >= nitems) return;
+
+    const FusedSeg &sg = segs[si];
+    const uint32_t p = sg.md.p, pinv = sg.md.pinv;
+    const int logNk = sg.logNk;
+    const int Lp = sg.Lp;
+    const int64_t g0 = (item - sg.item0) * S;
+    const int64_t row0 = g0 >> logNk;
+    const int64_t glast = min(g0 + S, sg.G) - 1;
+    const int nrows = (int)((glast >> logNk) - row0 + 1);
+
+    // 0. this item's Q rows into shared memory (contiguous in global memory)
+    {
+      const uint32_t *src = partial + sg.q_off + row0 * NN2 * (int64_t)Lp;
+      const int words = nrows * NN2 * Lp;
+      if ((Lp & 3) == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(qsm);
+        for (int w = threadIdx.x; w < (words >> 2); w += bd) d4[w] = __ldg(s4 + w);
+      } else {
+        for (int w = threadIdx.x; w < words; w += bd) qsm[w] = __ldg(src + w);
+      }
+    }
+    __syncthreads();
+
+    const int64_t g = g0 + team;
+    const bool active = g < sg.G;
+    const int64_t gg = active ? g : glast;
+    const int ik = (int)(gg & ((1 << logNk) - 1));
+    const int L = sg.L;
+    uint32_t X[8];
+    X[0] = sg.md.r1;
+    if (logNk == 0) {
+      X[1] = sg.md.r1;
+    } else {
+      const int h = 1 << (logNk - 1);
+      X[1] = (ik < h) ? __ldg(sg.tw + ik) : p - __ldg(sg.tw + (ik - h));
+    }
+#pragma unroll
+    for (int l = 2; l < 8; ++l) X[l] = (l < L) ? mmul(X[l - 1], X[1], p, pinv) : 0u;
+
+    // 1. entries of this lane's columns at its node, into its slice
+    uint32_t *mine = ent + threadIdx.x;
+    fused_eval_entries<NN, T>(qsm + ((gg >> logNk) - row0) * NN2 * Lp, t, X, L, Lp, p, pinv, mine,
+                              bd);
+    // 2. elimination in registers
+    fused_det<NN, T>(mine, bd, t, sg.md, sg.rn, active && t == 0, detvals + sg.det_off + g);
+  }
+}
+
+// Dynamic shared memory of a fused CTA: entry slices + `qwords` of Q rows.
+template <int NN>
+constexpr size_t fused_smem(int threads, size_t qwords) {
+  return (fused_slice_words<NN>(threads) + qwords) * sizeof(uint32_t);
+}
+
+template <int NN, int HI>
+static int fused_dispatch(int n, const FusedSeg *segs, int nsegs, int64_t nitems,
+                          const uint32_t *partial, uint32_t *detvals, unsigned long long *counter,
+                          int threads, int blocks, size_t qwords, cudaStream_t st) {
+  if (n == NN) {
+    fused_kernel<NN, TeamFor<NN>::value><<<blocks, threads, fused_smem<NN>(threads, qwords), st>>>(
+        segs, nsegs, (long long)nitems, partial, detvals, counter);
+    PD_CUDA(cudaGetLastError());
+    return POLYDET_OK;
+  }
+  if constexpr (NN < HI) {
+    return fused_dispatch<NN + 1, HI>(n, segs, nsegs, nitems, partial, detvals, counter, threads,
+                                      blocks, qwords, st);
+  }
+  return POLYDET_EINVAL;
+}
+
+// Occupancy of order n at `threads` lanes and `qwords` words of Q rows; also
+// raises the kernel's dynamic shared-memory limit (call before any graph
+// capture: the batch plan and polydet_batch_set_launch do).  Reports 0 when
+// the CTA does not fit.
+template <int NN, int HI>
+static int fused_occ_dispatch(int n, int threads, size_t qwords, int *bps) {
+  if (n == NN) {
+    const size_t smem = fused_smem<NN>(threads, qwords);
+    if (smem > 220 * 1024) {
+      *bps = 0;
+      return POLYDET_OK;
+    }
+    PD_CUDA(cudaFuncSetAttribute(fused_kernel<NN, TeamFor<NN>::value>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    PD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fused_kernel<NN, TeamFor<NN>::value>,
+                                                          threads, smem));
+    return POLYDET_OK;
+  }
+  if constexpr (NN < HI) return fused_occ_dispatch<NN + 1, HI>(n, threads, qwords, bps);
+  return POLYDET_EINVAL;
+}

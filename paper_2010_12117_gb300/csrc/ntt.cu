@@ -35,6 +35,10 @@ struct TxArgs {
   const uint32_t *ninv;
   int nvars, var;
   uint32_t *status;
+  // interleaved output (partial evaluation, A == 1): element (r, b) of entry
+  // e goes to ((r * (B / il_L) + b / il_L) * il_n2 + e) * il_Lp + b % il_L
+  int il_L, il_Lp;
+  int64_t il_n2;
 };
 
 __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
@@ -107,7 +111,13 @@ __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
     if (r < a.Lout) {
       if (a.inverse) v = mmul(scale, v, md.p, md.pinv);
       const int64_t aa = col / a.B, bb = col - aa * a.B;
-      a.out[out_base + (aa * a.Lout + r) * a.B + bb] = v;
+      if (a.il_L) {
+        const int64_t row = (int64_t)r * (a.B / a.il_L) + bb / a.il_L;
+        a.out[(int64_t)blockIdx.z * a.out_prime_stride + (row * a.il_n2 + blockIdx.y) * a.il_Lp +
+              bb % a.il_L] = v;
+      } else {
+        a.out[out_base + (aa * a.Lout + r) * a.B + bb] = v;
+      }
     } else if (a.inverse && v != 0u) {
       bad = true;
     }
@@ -244,6 +254,75 @@ extern "C" int polydet_interp(polydet_plan_t pl, const uint32_t *detvals, int lo
     if (rc) return rc;
     cur_in = a.out;
     cur_prime = a.out_prime_stride;
+  }
+  return POLYDET_OK;
+}
+
+uint64_t pd_partial_ws_words(const polydet_plan_s *pl) {
+  // pass v >= 1 output per entry: prod_{u<v} L_u * prod_{v<=u<k-1} N_u * L_{k-1}
+  const int k = pl->nvars;
+  uint64_t best = 0;
+  for (int v = 1; v <= k - 2; ++v) {
+    uint64_t s = (uint64_t)(pl->d[k - 1] + 1);
+    for (int u = 0; u < k - 1; ++u) s *= (u < v) ? (uint64_t)(pl->d[u] + 1) : (uint64_t)pl->N[u];
+    if (s > best) best = s;
+  }
+  return 2 * best * (uint64_t)pl->n * pl->n;
+}
+
+int pd_eval_partial(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int hi, uint32_t *out,
+                    int Lp, uint32_t *ws, cudaStream_t st) {
+  const int k = pl->nvars, np = hi - lo;
+  if (k < 2) return POLYDET_EINVAL;
+  const int64_t n2 = (int64_t)pl->n * pl->n;
+  const int Lk = pl->d[k - 1] + 1;
+  int64_t rows = 1;
+  for (int u = 0; u < k - 1; ++u) rows *= pl->N[u];
+  const uint64_t slot = pd_partial_ws_words(pl) / (2 * (uint64_t)n2);
+  const void *cur_in = coeffs;
+  int64_t cur_item = pl->E, cur_prime = 0;
+  int cur_i32 = 1;
+  int t = 0;
+  for (int v = k - 2; v >= 0; --v, ++t) {
+    TxArgs a = {};
+    a.A = 1;
+    for (int u = 0; u < v; ++u) a.A *= pl->d[u] + 1;
+    a.B = Lk;
+    for (int u = v + 1; u < k - 1; ++u) a.B *= pl->N[u];
+    a.Lin = pl->d[v] + 1;
+    a.N = pl->N[v];
+    a.logN = pl->logN[v];
+    a.Lout = a.N;
+    a.in = cur_in;
+    a.in_item_stride = cur_item;
+    a.in_prime_stride = cur_prime;
+    a.in_is_i32 = cur_i32;
+    if (v == 0) {
+      a.out = out;
+      a.out_prime_stride = rows * n2 * Lp;
+      a.il_L = Lk;
+      a.il_Lp = Lp;
+      a.il_n2 = n2;
+    } else {
+      a.out = ws + (uint64_t)(t % 2) * slot * (uint64_t)n2 * (uint64_t)np;
+      a.out_item_stride = (int64_t)slot;
+      a.out_prime_stride = n2 * (int64_t)slot;
+    }
+    a.prime_lo = lo;
+    a.mod = pl->d_mod;
+    a.tw = pl->d_tw_fwd;
+    a.tw_len = pl->tw_len;
+    a.tw_off = pl->tw_off[v];
+    a.ninv = pl->d_ninv;
+    a.nvars = k;
+    a.var = v;
+    a.status = pl->d_status;
+    int rc = launch_pass(a, (int)n2, np, st);
+    if (rc) return rc;
+    cur_in = a.out;
+    cur_item = a.out_item_stride;
+    cur_prime = a.out_prime_stride;
+    cur_i32 = 0;
   }
   return POLYDET_OK;
 }

@@ -233,6 +233,8 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
       ninv[(size_t)q * nvars + v] = h_mont(h_powmod(N % p, p - 2, p), p);
     }
     rn[q] = h_powmod(mod[q].r1, (uint64_t)n, p);  // (R mod p)^n = R^n mod p
+    pl->mod_h[q] = mod[q];
+    pl->rn_h[q] = rn[q];
   }
 
   // Garner tables (Sec. 3.4 with the standard reading of its constants):

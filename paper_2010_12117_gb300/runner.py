@@ -156,3 +156,127 @@ class PlainRunner:
     def close(self) -> None:
         for pl in self.plans:
             pl.close()
+
+
+class BatchedRunner:
+    """The batched form: every job of the list in one fused run (partial
+    evaluation, one persistent fused kernel per matrix order, interpolation,
+    CRT), optionally captured once in a CUDA graph and replayed."""
+
+    def __init__(self, mats: Sequence, nprimes: Optional[Sequence[int]] = None,
+                 device: str = "cuda", tune: bool = True, stream: Optional[torch.cuda.Stream] = None):
+        from .binding import Batch
+        self.mats = list(mats)
+        Ps = [nprimes[i] if nprimes is not None else prime_count(pm.coeffs)
+              for i, pm in enumerate(self.mats)]
+        self.batch = Batch([(pm.n, pm.degs, P) for pm, P in zip(self.mats, Ps)])
+        self.dev = torch.device(device)
+        w = self.batch.words
+        self.coeffs_dev = torch.empty(max(1, w["coeffs"]), dtype=torch.int32, device=self.dev)
+        self.partial = torch.empty(max(1, w["partial"]), dtype=torch.int32, device=self.dev)
+        self.detvals = torch.empty(max(1, w["detvals"]), dtype=torch.int32, device=self.dev)
+        self.residues = torch.empty(max(1, w["residues"]), dtype=torch.int32, device=self.dev)
+        self.limbs = torch.empty(max(1, w["limbs"]), dtype=torch.int32, device=self.dev)
+        self.ws = torch.empty(max(1, w["workspace"]), dtype=torch.int32, device=self.dev)
+        self.host_in = torch.empty(max(1, w["coeffs"]), dtype=torch.int32, pin_memory=True)
+        self.host_out = torch.empty(max(1, w["limbs"]), dtype=torch.int32, pin_memory=True)
+        co = self.batch.offsets["coeffs"]
+        for i, pm in enumerate(self.mats):
+            self.host_in[co[i]:co[i + 1]] = torch.from_numpy(
+                np.ascontiguousarray(pm.coeffs, dtype=np.int32).reshape(-1))
+        self.graph = None
+        self.tuning = {}
+        st = stream or torch.cuda.current_stream()
+        if tune:
+            self.upload(st)
+            self.batch.eval(self.coeffs_dev, self.partial, self.ws, st)
+            from .tune import tune as _tune
+            self.tuning = _tune(self.batch, self.partial, self.detvals, self.ws, st)
+
+    @property
+    def h2d_bytes(self) -> int:
+        return 4 * self.batch.words["coeffs"]
+
+    @property
+    def d2h_bytes(self) -> int:
+        return 4 * self.batch.words["limbs"]
+
+    def modp_dets(self) -> int:
+        return sum(int(i.P) * int(i.G) for i in self.batch.job_info)
+
+    def updates(self) -> int:
+        return sum(int(i.P) * int(i.G) * condense_updates(int(i.n)) for i in self.batch.job_info)
+
+    def kernel_launches(self) -> int:
+        tot = 0
+        for i in self.batch.job_info:
+            tot += max(1, int(i.nvars) - 1)  # partial evaluation passes (or the repack)
+            tot += int(i.nvars) + 1          # interpolation passes and CRT
+        return tot + len(self.batch.orders())
+
+    def upload(self, stream: torch.cuda.Stream) -> None:
+        with torch.cuda.stream(stream):
+            self.coeffs_dev.copy_(self.host_in, non_blocking=True)
+
+    def _stages(self, stream):
+        b = self.batch
+        return [("eval", lambda: b.eval(self.coeffs_dev, self.partial, self.ws, stream),
+                 4.0 * (b.words["coeffs"] + b.words["partial"])),
+                ("fused", lambda: b.condense(self.partial, self.detvals, self.ws, stream),
+                 float(self.updates())),
+                ("interp", lambda: b.interp(self.detvals, self.residues, self.ws, stream),
+                 4.0 * (b.words["detvals"] + b.words["residues"])),
+                ("crt", lambda: b.crt(self.residues, self.limbs, stream),
+                 4.0 * (b.words["residues"] + b.words["limbs"]))]
+
+    def capture(self, stream: torch.cuda.Stream) -> None:
+        """Capture each stage of one run in its own CUDA graph; compute()
+        then replays the four graphs (stage events go between them)."""
+        for _, fn, _ in self._stages(stream):  # warm: kernel attributes set before capture
+            fn()
+        stream.synchronize()
+        graphs = []
+        for name, _, work in self._stages(stream):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                cur = torch.cuda.current_stream()
+                dict((n, f) for n, f, _ in self._stages(cur))[name]()
+            graphs.append((name, g, work))
+        self.graph = graphs
+
+    def compute(self, stream: torch.cuda.Stream, timer: Optional[StageTimer] = None) -> None:
+        if self.graph is not None:
+            with torch.cuda.stream(stream):
+                for name, g, work in self.graph:
+                    if timer is None:
+                        g.replay()
+                    else:
+                        timer.run(name, stream, g.replay, work)
+            return
+        for name, fn, work in self._stages(stream):
+            if timer is None:
+                fn()
+            else:
+                timer.run(name, stream, fn, work)
+
+    def download(self, stream: torch.cuda.Stream) -> None:
+        with torch.cuda.stream(stream):
+            self.host_out.copy_(self.limbs, non_blocking=True)
+
+    def check_status(self, stream: torch.cuda.Stream) -> None:
+        st = self.batch.sync_status(stream)
+        if st:
+            raise PolydetError(EBOUND, f"device status {st:#x}")
+
+    def results(self) -> List[List[int]]:
+        out = []
+        host = self.host_out.numpy().view(np.uint32)
+        lo = self.batch.offsets["limbs"]
+        for j, info in enumerate(self.batch.job_info):
+            C, W = int(info.C), int(info.W)
+            out.append(limbs_to_ints(host[lo[j]:lo[j + 1]].reshape(C, W), W))
+        return out
+
+    def close(self) -> None:
+        self.graph = None
+        self.batch.close()

@@ -1,0 +1,128 @@
+"""The batched form (fused last-variable evaluation + condensation, one
+persistent kernel per matrix order, CUDA graph) against the plain per-matrix
+GPU form and the CPU oracle: identical integers."""
+import numpy as np
+import pytest
+
+from helpers import ensure_lib
+from oracle import bareiss, certificate
+from oracle import poly as P_
+from paper_2010_12117_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ensure_lib()
+
+
+def batched_results(mats, tune=False, graph=False, replays=1):
+    from paper_2010_12117_gb300.runner import BatchedRunner
+    st = torch.cuda.Stream()
+    r = BatchedRunner(mats, tune=tune, stream=st)
+    r.upload(st)
+    if graph:
+        r.capture(st)
+    for _ in range(replays):
+        r.compute(st)
+    r.download(st)
+    st.synchronize()
+    r.check_status(st)
+    out = r.results()
+    r.close()
+    return out
+
+
+def plain(pm):
+    from paper_2010_12117_gb300.pipeline import determinant
+    return determinant(pm.coeffs, pm.degs).coeffs
+
+
+def _mixed():
+    rng = np.random.default_rng(4242)
+    mats = []
+    for n, degs, dens in [(1, (3,), 1.0), (2, (1, 1), 1.0), (3, (2, 0, 1), 0.8), (4, (2, 2), 0.5),
+                          (5, (1, 2, 1), 0.4), (6, (4,), 0.3), (7, (1, 1), 0.6), (8, (2,), 1.0),
+                          (9, (1, 1, 1), 0.3), (10, (1,), 0.5), (11, (1, 2), 0.3), (12, (1, 1, 1), 0.3),
+                          (13, (2,), 0.6), (14, (1,), 1.0), (16, (1, 1), 0.3), (17, (1,), 0.7),
+                          (20, (1, 1), 0.3), (21, (2,), 0.5), (24, (1,), 0.4), (25, (1,), 1.0),
+                          (28, (1,), 0.3), (32, (1,), 0.5), (4, (7,), 1.0), (6, (1, 7), 0.5)]:
+        mats.append(synth.random_matrix(rng, n, degs, dens, -300, 300))
+    return mats
+
+
+def test_mixed_orders_match_plain_and_oracle():
+    mats = _mixed()
+    got = batched_results(mats)
+    for pm, g in zip(mats, got):
+        assert g == plain(pm), (pm.n, pm.degs)
+        cost = pm.n ** 3 * np.prod([pm.n * d + 1 for d in pm.degs])
+        if cost < 2e6:
+            assert g == bareiss.det_packed(pm.coeffs.tolist(), pm.degs), (pm.n, pm.degs)
+
+
+def test_graph_replay_and_tuning_do_not_change_results():
+    mats = _mixed()[:12]
+    a = batched_results(mats)
+    b = batched_results(mats, tune=True, graph=True, replays=3)
+    assert a == b
+
+
+def test_batched_workload_members_match_plain():
+    mats = synth.batched(0, 256)[:40]
+    got = batched_results(mats, tune=True, graph=True)
+    for pm, g in zip(mats, got):
+        assert g == plain(pm), pm.name
+        cost = pm.n ** 3 * np.prod([pm.n * d + 1 for d in pm.degs])
+        if cost < 1e6:
+            assert g == bareiss.det_packed(pm.coeffs.tolist(), pm.degs), pm.name
+
+
+def test_structured_and_singular_jobs():
+    """Zero pivots (Sylvester, anti-diagonal), rank deficiency and zero
+    matrices inside one batch."""
+    k = 2
+    rng = np.random.default_rng(9)
+    mats = [synth.sylvester_16(5)]
+    a = np.zeros((6, 6, 2), dtype=np.int64)
+    for i in range(6):
+        a[i, 5 - i] = [i + 1, 1]
+    mats.append(synth.PolyMatrix(6, (1,), a))
+    pm = synth.random_matrix(rng, 5, (2, 2), 0.8, -9, 10)
+    M = P_.matrix_from_dense(pm.coeffs.tolist(), pm.degs)
+    x = P_.var(0, k)
+    M[3] = [P_.add(P_.mul(x, M[0][j]), M[2][j]) for j in range(5)]
+    c = np.array([[P_.to_dense(M[i][j], (3, 2)) for j in range(5)] for i in range(5)], dtype=np.int64)
+    mats.append(synth.PolyMatrix(5, (3, 2), c))
+    mats.append(synth.PolyMatrix(7, (1, 1, 1), np.zeros((7, 7, 8), dtype=np.int64)))
+    got = batched_results(mats)
+    assert got[0] == bareiss.det_packed(mats[0].coeffs.tolist(), mats[0].degs)
+    want = P_.const(-1, 1)
+    for i in range(6):
+        want = P_.mul(want, {(0,): i + 1, (1,): 1})
+    assert P_.from_dense(got[1], (6,)) == want
+    assert not any(got[2]) and not any(got[3])
+
+
+def test_large_served_job_in_a_mix():
+    """A 32x32 job over Z[x, y] with degree 6 (the served workload's large
+    jobs) batched with small ones: equal to the plain path, certified."""
+    rng = np.random.default_rng(1)
+    big = synth.large_32x32_xy(rng)
+    mats = [big] + synth.batched(7, 6)
+    got = batched_results(mats)
+    want_big = plain(big)
+    assert got[0] == want_big
+    from oracle import plan as oplan
+    assert certificate.check(big.coeffs.tolist(), big.degs, got[0],
+                             oplan.det_degree_bound(32, big.degs), trials=1)
+    for pm, g in zip(mats[1:], got[1:]):
+        assert g == plain(pm)
+
+
+def test_last_variable_degree_limit():
+    from paper_2010_12117_gb300.binding import Batch, PolydetError
+    with pytest.raises(PolydetError):
+        Batch([(4, (1, 8), 2)])
