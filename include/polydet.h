@@ -135,6 +135,36 @@ int polydet_condense_batch(polydet_plan_t plan, const uint32_t *evals_dev,
 int polydet_interp(polydet_plan_t plan, const uint32_t *detvals_dev, int prime_lo,
                    int prime_hi, uint32_t *residues_dev, uint32_t *ws_dev, void *stream);
 
+/* Interpolation without any device allocation (the paper has no counterpart;
+ * this exists for callers of the library).
+ * Some callers cannot call cudaMalloc when they need the result: code that
+ * runs while a stream is being captured into a CUDA graph in the global
+ * capture mode (where cudaMalloc is not permitted), processes whose device
+ * memory is reserved up front by another allocator or memory pool, and
+ * latency-bound loops that must not stall on cudaMalloc/cudaFree (both
+ * synchronise the device).  polydet_interp_static does exactly what
+ * polydet_interp does, with its scratch taken from a file-scope device array
+ * of POLYDET_STATIC_SCRATCH_WORDS words (16 MiB) instead of a caller
+ * workspace.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - Every GPU that loads the library holds that array until the process
+ *    exits.
+ *  - The first call on a device (with that device current) looks up the
+ *    array's device address once; make that first call before any stream
+ *    capture.
+ *  - Requests needing more than the array, i.e. (prime_hi - prime_lo) *
+ *    info.interp_ws_words > POLYDET_STATIC_SCRATCH_WORDS, return
+ *    POLYDET_ETOOBIG and enqueue nothing: split the prime range.
+ *  - All calls share the one array and it keeps the last call's contents
+ *    (nothing in it needs clearing: each pass overwrites what the next reads).
+ *    Calls that overlap on the GPU - on different streams, or from different
+ *    threads - race on it: issue them on one stream, or use polydet_interp
+ *    with separate workspaces.
+ * Arguments, layouts and the status word are as for polydet_interp. */
+#define POLYDET_ETOOBIG (-8) /* request larger than a fixed internal buffer */
+#define POLYDET_STATIC_SCRATCH_WORDS (4u * 1024u * 1024u)
+int polydet_interp_static(polydet_plan_t plan, const uint32_t *detvals_dev, int prime_lo,
+                          int prime_hi, uint32_t *residues_dev, void *stream);
+
 /* Stage 4, CRT (Sec. 3.4, Algorithm 4): mixed-radix (Garner) digits of each
  * coefficient over all P primes, converted to the signed integer in
  * (-M/2, M/2), M = prod p.  residues_dev: device uint32 [P][C]; limbs_dev:

@@ -20,8 +20,10 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libpolydet.so")
 
 MAX_VARS = 6
 OK, EINVAL, EDEGREE, EPRIMES, ENOMEM, ECUDA, ETIMEOUT, EBOUND = 0, -1, -2, -3, -4, -5, -6, -7
+ETOOBIG = -8
+STATIC_SCRATCH_WORDS = 4 * 1024 * 1024
 _ERRNAMES = {EINVAL: "EINVAL", EDEGREE: "EDEGREE", EPRIMES: "EPRIMES", ENOMEM: "ENOMEM",
-             ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", EBOUND: "EBOUND"}
+             ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", EBOUND: "EBOUND", ETOOBIG: "ETOOBIG"}
 
 
 class PolydetError(RuntimeError):
@@ -74,6 +76,7 @@ SIGNATURES = {
     "polydet_eval": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP]),
     "polydet_condense_batch": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
     "polydet_interp": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP]),
+    "polydet_interp_static": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
     "polydet_crt": (_I, [_VP, _VP, _VP, _VP]),
     "polydet_sync_status": (_I, [_VP, _VP, _PU32]),
     "polydet_batch_plan": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(Job), _I, _U32]),
@@ -235,6 +238,15 @@ class Plan:
             _ptr(residues, torch.int32, (hi - lo) * self.C, "residues"),
             self._ws(ws, self.interp_ws_words, hi - lo, "polydet_interp"), _stream(stream)),
             "polydet_interp")
+
+    def interp_static(self, detvals: torch.Tensor, lo: int, hi: int, residues: torch.Tensor,
+                      stream=None) -> None:
+        """polydet_interp without a workspace: scratch from the library's
+        fixed device array (for callers that cannot allocate)."""
+        _check(lib().polydet_interp_static(
+            self._h, _ptr(detvals, torch.int32, (hi - lo) * self.G, "detvals"), lo, hi,
+            _ptr(residues, torch.int32, (hi - lo) * self.C, "residues"), _stream(stream)),
+            "polydet_interp_static")
 
     def crt(self, residues: torch.Tensor, limbs: torch.Tensor, stream=None) -> None:
         _check(lib().polydet_crt(self._h, _ptr(residues, torch.int32, self.P * self.C, "residues"),
