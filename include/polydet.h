@@ -252,6 +252,34 @@ int polydet_batch_crt(polydet_batch_t batch, const uint32_t *residues_dev, uint3
 /* OR of every job's status word (synchronises; clears them). */
 int polydet_batch_sync_status(polydet_batch_t batch, void *stream, uint32_t *status_out);
 
+/* ------------------------------------------------------------------------
+ * Run-time / memory predictor for scheduling (generalises the prediction of
+ * Sec. 5, T = C_p r^2 Round(mean T_e, 2) mu): an fp32 MLP 8 -> 64 -> 64 -> 2
+ * with ReLU.  Parameters are one device float array of POLYDET_MLP_PARAMS:
+ * W1[64][8] b1[64] W2[64][64] b2[64] W3[2][64] b3[2] (row = output unit).
+ * Loss: L = 1/(2B) sum_b sum_o (y_bo - t_bo)^2.  All pointers are device
+ * memory owned by the caller; nothing is allocated.
+ * ------------------------------------------------------------------------ */
+#define POLYDET_MLP_IN 8
+#define POLYDET_MLP_HIDDEN 64
+#define POLYDET_MLP_OUT 2
+#define POLYDET_MLP_PARAMS 4866
+/* y[B][2] = MLP(x[B][8]).  act_ws: [B][128] floats receiving the hidden
+ * activations (needed by polydet_mlp_backward), or NULL for inference. */
+int polydet_mlp_forward(const float *params, const float *x, int batch, float *y, float *act_ws,
+                        void *stream);
+/* Gradient of L at (x, target) after polydet_mlp_forward wrote y and act_ws:
+ * grads[POLYDET_MLP_PARAMS] (overwritten), *loss (device float, may be
+ * NULL); delta_ws: [B][130] floats of scratch.  Deterministic: every sum runs
+ * over the batch in sample order. */
+int polydet_mlp_backward(const float *params, const float *x, const float *target, int batch,
+                         const float *y, const float *act_ws, float *delta_ws, float *grads,
+                         float *loss, void *stream);
+/* One Adam step (bias-corrected, step >= 1) with decoupled weight decay:
+ * p -= lr * (m_hat / (sqrt(v_hat) + eps) + weight_decay * p). */
+int polydet_mlp_adam(float *params, const float *grads, float *m, float *v, int step, float lr,
+                     float beta1, float beta2, float eps, float weight_decay, void *stream);
+
 /* Measurement utility (not a stage of the method): runs two in-register
  * integer streams on every SM and reports their rates, the ceilings of the
  * condensation kernels - plain 32-bit multiply-adds per second, and fused

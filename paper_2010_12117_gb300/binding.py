@@ -91,6 +91,10 @@ SIGNATURES = {
     "polydet_batch_interp": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "polydet_batch_crt": (_I, [_VP, _VP, _VP, _VP]),
     "polydet_batch_sync_status": (_I, [_VP, _VP, _PU32]),
+    "polydet_mlp_forward": (_I, [_VP, _VP, _I, _VP, _VP, _VP]),
+    "polydet_mlp_backward": (_I, [_VP, _VP, _VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "polydet_mlp_adam": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_float, ctypes.c_float, _VP]),
     "polydet_probe_int_peaks": (_I, [_VP, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]),
     "polydet_last_error": (ctypes.c_char_p, []),
@@ -344,6 +348,38 @@ class Batch:
         if rc not in (OK, EBOUND, ETIMEOUT):
             _check(rc, "polydet_batch_sync_status")
         return st.value
+
+
+MLP_PARAMS = 4866
+
+
+def _fptr(t: torch.Tensor, numel: int, name: str) -> ctypes.c_void_p:
+    return _ptr(t, torch.float32, numel, name)
+
+
+def mlp_forward(params, x, y, act=None, stream=None) -> None:
+    B = x.shape[0]
+    _check(lib().polydet_mlp_forward(_fptr(params, MLP_PARAMS, "params"), _fptr(x, B * 8, "x"), B,
+                                     _fptr(y, B * 2, "y"),
+                                     _fptr(act, B * 128, "act") if act is not None else None,
+                                     _stream(stream)), "polydet_mlp_forward")
+
+
+def mlp_backward(params, x, target, y, act, delta, grads, loss=None, stream=None) -> None:
+    B = x.shape[0]
+    _check(lib().polydet_mlp_backward(
+        _fptr(params, MLP_PARAMS, "params"), _fptr(x, B * 8, "x"), _fptr(target, B * 2, "target"), B,
+        _fptr(y, B * 2, "y"), _fptr(act, B * 128, "act"), _fptr(delta, B * 130, "delta"),
+        _fptr(grads, MLP_PARAMS, "grads"), _fptr(loss, 1, "loss") if loss is not None else None,
+        _stream(stream)), "polydet_mlp_backward")
+
+
+def mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0,
+             stream=None) -> None:
+    _check(lib().polydet_mlp_adam(_fptr(params, MLP_PARAMS, "params"), _fptr(grads, MLP_PARAMS, "grads"),
+                                  _fptr(m, MLP_PARAMS, "m"), _fptr(v, MLP_PARAMS, "v"), int(step),
+                                  float(lr), float(beta1), float(beta2), float(eps),
+                                  float(weight_decay), _stream(stream)), "polydet_mlp_adam")
 
 
 def probe_int_peaks(stream=None) -> tuple[float, float]:

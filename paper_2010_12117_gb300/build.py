@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libpolydet.so")
 
-SOURCES = ["plan.cu", "ntt.cu", "crt.cu", "probe.cu", "batch.cu", "dispatch.cu", "interp_static.cu"]
+SOURCES = ["plan.cu", "ntt.cu", "crt.cu", "probe.cu", "batch.cu", "dispatch.cu", "interp_static.cu", "mlp.cu"]
 # condense_inst.cu and fused_inst.cu are compiled once per range of matrix
 # orders (must match the ranges in csrc/dispatch.cu)
 KERNEL_RANGES = [(1, 6), (7, 10), (11, 12), (13, 16), (17, 20), (21, 24), (25, 28), (29, 32)]

@@ -1,0 +1,185 @@
+"""Run-time and device-memory prediction for determinant jobs.
+
+The paper predicts the run time of a job as T = C_p r^2 Round(mean T_e, 2) mu
+(Sec. 5): primes x entries x the mean per-entry FFT time x a replication
+factor.  Here the same idea is carried to the batched GPU form in two layers:
+
+* ``analytic`` - a bound from the job's shape alone: prime count from the
+  Hadamard bound, grid and output sizes, the exact buffer bytes of the
+  batched form (memory), and a roofline time, max(updates / integer-pipe
+  rate, bytes / HBM rate) plus a per-launch cost.  It needs no training and
+  is a lower bound of both quantities.
+* ``Predictor`` - an fp32 MLP 8 -> 64 -> 64 -> 2 trained on the method's own
+  measured timings and footprints, with forward, backward and Adam in the
+  library's CUDA kernels.  Inputs: n, k, max and mean degree, density,
+  coefficient bits, and the logs of the analytic time and memory; outputs:
+  log time and log memory (standardised).  The analytic bound judges it:
+  a prediction below the bound is raised to it, one more than ``max_ratio``
+  times the bound falls back to the bound times the calibrated median ratio,
+  and an untrained predictor answers with that calibrated bound.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import binding
+
+UPDATE_RATE = 3.0e12      # fused updates/s, the probe's ceiling on GB300
+HBM_RATE = 6.786e12       # bytes/s, measured copy bandwidth
+LAUNCH_S = 4e-6           # per kernel launch inside a graph
+
+
+def _nextpow2(x: int) -> int:
+    n = 1
+    while n < x:
+        n *= 2
+    return n
+
+
+@dataclass
+class Shape:
+    n: int
+    degs: tuple
+    P: int
+    density: float
+    coef_bits: float
+
+    @property
+    def k(self) -> int:
+        return len(self.degs)
+
+
+def shape_of(pm) -> Shape:
+    from .pipeline import prime_count
+    c = np.asarray(pm.coeffs)
+    nz = float((c != 0).mean()) if c.size else 0.0
+    bits = math.log2(float(np.abs(c).max(initial=0)) + 1.0)
+    return Shape(pm.n, tuple(int(d) for d in pm.degs), prime_count(c), nz, bits)
+
+
+def analytic(s: Shape) -> tuple:
+    """(seconds, bytes): roofline time and exact buffer bytes of the batched form."""
+    n, k, P = s.n, s.k, s.P
+    D = [n * d for d in s.degs]
+    N = [_nextpow2(x + 1) for x in D]
+    G = math.prod(N)
+    C = math.prod(x + 1 for x in D)
+    E = math.prod(d + 1 for d in s.degs)
+    L = s.degs[-1] + 1
+    Lp = _nextpow2(L)
+    rows = G // N[-1]
+    W = max(1, math.ceil(P * 30.99 / 32))
+    n2 = n * n
+    partial = P * rows * n2 * Lp
+    pws = 0
+    if k > 2:
+        for v in range(1, k - 1):
+            sz = L
+            for u in range(k - 1):
+                sz *= (s.degs[u] + 1) if u < v else N[u]
+            pws = max(pws, sz)
+        pws *= 2 * n2
+    iws = 0
+    for v in range(1, k):
+        sz = 1
+        for u in range(k):
+            sz *= N[u] if u < v else (D[u] + 1)
+        iws = max(iws, sz)
+    iws *= 2
+    words = n2 * E + partial + P * G + P * C + C * W + 256 + P * max(pws, iws)
+    mem = 4 * words
+    updates = P * G * (n - 1) * n * (2 * n - 1) // 6
+    moved = 4 * (2 * partial + 2 * P * G + P * C + C * W)
+    launches = max(1, k - 1) + k + 2
+    t = max(updates / UPDATE_RATE, moved / HBM_RATE) + launches * LAUNCH_S
+    return t, float(mem)
+
+
+def features(s: Shape) -> np.ndarray:
+    t, m = analytic(s)
+    return np.array([s.n / 32.0, s.k / 6.0, max(s.degs) / 8.0, float(np.mean(s.degs)) / 8.0,
+                     s.density, s.coef_bits / 32.0, math.log10(t) / 4.0 + 1.0, math.log2(m) / 40.0],
+                    dtype=np.float32)
+
+
+class Predictor:
+    """The MLP, its training loop and the analytic judge."""
+
+    def __init__(self, seed: int = 0, device: str = "cuda", max_ratio: float = 50.0):
+        self.dev = torch.device(device)
+        self.params = torch.from_numpy(init_params(seed)).to(self.dev)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+        self.mu = np.zeros(2, dtype=np.float32)
+        self.sd = np.ones(2, dtype=np.float32)
+        self.ratio = np.ones(2, dtype=np.float64)  # calibrated median actual / bound
+        self.trained = False
+        self.max_ratio = max_ratio
+
+    # -- training ----------------------------------------------------------
+    def fit(self, X: np.ndarray, Y: np.ndarray, bounds: np.ndarray, steps: int = 1500,
+            lr: float = 3e-3, weight_decay: float = 1e-4) -> List[float]:
+        """X [B][8] features, Y [B][2] measured (seconds, bytes), bounds [B][2]
+        analytic (seconds, bytes).  Full-batch Adam on the GPU kernels."""
+        logy = np.log(np.maximum(Y, 1e-12)).astype(np.float64)
+        self.mu = logy.mean(0).astype(np.float32)
+        self.sd = np.maximum(logy.std(0), 1e-3).astype(np.float32)
+        self.ratio = np.exp(np.median(logy - np.log(bounds), axis=0))
+        T = ((logy - self.mu) / self.sd).astype(np.float32)
+        B = len(X)
+        x = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(self.dev)
+        t = torch.from_numpy(np.ascontiguousarray(T)).to(self.dev)
+        y = torch.empty(B, 2, device=self.dev)
+        act = torch.empty(B, 128, device=self.dev)
+        delta = torch.empty(B, 130, device=self.dev)
+        grads = torch.empty(binding.MLP_PARAMS, device=self.dev)
+        loss = torch.empty(1, device=self.dev)
+        hist = []
+        for it in range(steps):
+            binding.mlp_forward(self.params, x, y, act)
+            binding.mlp_backward(self.params, x, t, y, act, delta, grads, loss)
+            self.step += 1
+            binding.mlp_adam(self.params, grads, self.m, self.v, self.step, lr,
+                             weight_decay=weight_decay)
+            if it % 100 == 0 or it == steps - 1:
+                hist.append(float(loss.item()))
+        self.trained = True
+        return hist
+
+    # -- inference -----------------------------------------------------------
+    def raw(self, X: np.ndarray) -> np.ndarray:
+        """MLP outputs mapped back to (seconds, bytes), unjudged."""
+        x = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(self.dev)
+        y = torch.empty(len(X), 2, device=self.dev)
+        binding.mlp_forward(self.params, x, y, None)
+        out = y.cpu().numpy().astype(np.float64) * self.sd + self.mu
+        return np.exp(out)
+
+    def predict(self, shapes: Sequence[Shape]) -> np.ndarray:
+        """Judged predictions [len][2] = (seconds, bytes)."""
+        bounds = np.array([analytic(s) for s in shapes], dtype=np.float64)
+        if not self.trained or len(shapes) == 0:
+            return bounds * self.ratio
+        X = np.stack([features(s) for s in shapes])
+        pred = self.raw(X)
+        pred = np.maximum(pred, bounds)
+        bad = pred > self.max_ratio * bounds
+        pred[bad] = (bounds * self.ratio)[bad]
+        return pred
+
+
+def init_params(seed: int) -> np.ndarray:
+    """He-uniform weights, zero biases, in the flat layout of polydet.h."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((8, 64), (64, 64), (64, 2)):
+        lim = math.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, (fan_out, fan_in)).ravel())
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)

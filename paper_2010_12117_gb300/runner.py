@@ -187,7 +187,10 @@ class BatchedRunner:
         self.graph = None
         self.tuning = {}
         st = stream or torch.cuda.current_stream()
-        if tune:
+        if tune == "cache":  # apply earlier choices of the autotuner, search nothing
+            from .tune import apply_cached
+            self.tuning = apply_cached(self.batch)
+        elif tune:
             self.upload(st)
             self.batch.eval(self.coeffs_dev, self.partial, self.ws, st)
             from .tune import tune as _tune
@@ -277,6 +280,14 @@ class BatchedRunner:
             out.append(limbs_to_ints(host[lo[j]:lo[j + 1]].reshape(C, W), W))
         return out
 
-    def close(self) -> None:
+    def release_buffers(self) -> None:
+        """Return the device buffers to torch's caching allocator (stream
+        ordered, no device synchronisation); the batch's small plan tables
+        stay until close()."""
         self.graph = None
+        for name in ("coeffs_dev", "partial", "detvals", "residues", "limbs", "ws"):
+            setattr(self, name, None)
+
+    def close(self) -> None:
+        self.release_buffers()
         self.batch.close()

@@ -49,6 +49,18 @@ def _key(n: int, items: int) -> str:
     return f"{dev}/n{n}/items2^{int(math.log2(max(1, items)))}"
 
 
+def apply_cached(batch) -> Dict[int, dict]:
+    """Set every order that has a cached choice; leave the others alone."""
+    cache = _load()
+    out = {}
+    for n in batch.orders():
+        key = _key(n, int(batch.info.items[n]))
+        if key in cache:
+            batch.set_launch(n, cache[key]["threads"])
+            out[n] = dict(cache[key], cached=True)
+    return out
+
+
 def tune(batch, partial, detvals, ws, stream: Optional[torch.cuda.Stream] = None,
          reps: int = 2, use_cache: bool = True) -> Dict[int, dict]:
     """Pick the CTA size of every order in ``batch`` (a binding.Batch whose
