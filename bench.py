@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--count", type=int, default=256)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-kernels", action="store_true")
+    ap.add_argument("--served-jobs", type=int, default=300)
     return ap.parse_args()
 
 
@@ -224,6 +227,89 @@ def _timed_steps(runner, st, flush, steps, stage_timer):
     return sum(s.elapsed_time(e) for s, e in marks)
 
 
+def served_leg(args, mats, batched_value, st):
+    """The served workload: a seeded Poisson stream of the batched
+    distribution plus 5 % 32x32 jobs over Z[x, y] (degree 6), at 60 % of the
+    batched throughput; continuous batching with admission by predicted
+    memory.  Once with the MLP trained on the method's own timings, once with
+    the analytic bound alone (same stream)."""
+    import numpy as np
+    from paper_2010_12117_gb300 import synth
+    from paper_2010_12117_gb300.predictor import Predictor
+    from paper_2010_12117_gb300.serve import Server, calibrate
+    rng = np.random.default_rng(args.seed + 1000)
+    cal = synth.batched(args.seed + 100, 60) + [synth.large_32x32_xy(rng) for _ in range(4)]
+    t0 = time.perf_counter()
+    X, Y, Bd = calibrate(cal, st)
+    pr = Predictor(seed=args.seed)
+    pr.fit(X, Y, Bd, steps=2000)
+    train_s = time.perf_counter() - t0
+    rate = 0.6 * batched_value
+    stream = synth.served_stream(args.seed, args.served_jobs, rate=rate)
+    out = {"rate_jobs_per_s": rate, "jobs": args.served_jobs, "calibration_jobs": len(cal),
+           "calibrate_and_train_s": train_s, "budget_bytes": 40e9, "slots": 3}
+    for name, p in (("mlp", pr), ("analytic", Predictor(seed=args.seed))):
+        srv = Server(p, mem_budget=40e9, slots=3, wave_seconds=0.02)
+        rep = srv.run(stream, keep_results=False)
+        out[name] = rep.summary()
+    return out
+
+
+def kernel_leg(st, hbm_peak):
+    """HBM-bound stages alone on inputs larger than L2: the eval NTT on the
+    12x12 trivariate grid (64^3 nodes, 5 primes: 755 MB written) and the CRT
+    on 2^24 coefficients with 6 and 11 primes."""
+    import numpy as np
+    import torch
+    from paper_2010_12117_gb300 import synth
+    from paper_2010_12117_gb300.binding import Plan
+
+    def timed(fn, reps=5):
+        fn()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(st)
+        for _ in range(reps):
+            fn()
+        e.record(st)
+        e.synchronize()
+        return s.elapsed_time(e) / reps
+
+    out = {}
+    pm = synth.sparse_12x12_xyz(0)
+    P = 5
+    pl = Plan(pm.n, pm.degs, P)
+    c = torch.from_numpy(pm.coeffs.astype(np.int32).reshape(-1)).cuda()
+    ev = torch.empty(P * pm.n * pm.n * pl.G, dtype=torch.int32, device="cuda")
+    ws = pl.workspace(P)
+    ms = timed(lambda: pl.eval(c, 0, P, ev, ws, st))
+    byts = 4.0 * P * pm.n * pm.n * (pl.E + pl.G)
+    out["eval_ntt_12x12_xyz"] = {"ms": ms, "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak,
+                                 "algorithmic_bytes": byts}
+    dv = torch.empty(P * pl.G, dtype=torch.int32, device="cuda")
+    pl.condense(ev, 0, P, dv, st)
+    rs = torch.empty(P * pl.C, dtype=torch.int32, device="cuda")
+    ms = timed(lambda: pl.interp(dv, 0, P, rs, ws, st))
+    byts = 4.0 * P * (pl.G + pl.C)
+    out["interp_ntt_12x12_xyz"] = {"ms": ms, "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak,
+                                   "algorithmic_bytes": byts}
+    pl.close()
+    del ev, ws, dv, rs
+    for P in (6, 11):
+        pc = Plan(1, (4095, 4095), P)  # C = 4096^2 = 2^24 coefficients
+        C = pc.C
+        res = torch.randint(0, 2 ** 30, (P * C,), dtype=torch.int32, device="cuda")
+        limbs = torch.empty(C * pc.W, dtype=torch.int32, device="cuda")
+        ms = timed(lambda: pc.crt(res, limbs, st))
+        byts = 4.0 * C * (P + pc.W)
+        out[f"crt_2^24_P{P}"] = {"ms": ms, "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak,
+                                 "algorithmic_bytes": byts, "W": pc.W}
+        pc.close()
+        del res, limbs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2010_12117_gb300 import synth
@@ -332,6 +418,9 @@ def run_ours(args, world, rank, local):
     roof = dict(roofs[dom], kernel="fused_kernel" if dom == "fused" else dom,
                 ms_in_timed_region=stage_ms[dom])
 
+    served = None if args.no_served else served_leg(args, mats, value, st)
+    kernels = None if args.no_kernels else kernel_leg(st, hbm_peak)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         done, el, skipped = oracle_sample(mats, args.cpu_seconds)
@@ -363,6 +452,8 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
+        "served": served,
+        "hbm_kernels": kernels,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
