@@ -25,9 +25,11 @@
  * Grid and coefficient layouts (Sec. 2, dense encoding, x1 slowest):
  *  - entry coefficients: int32 [n][n][E], E = prod_v (d_v + 1), exponent
  *    vectors (e1..ek) with 0 <= e_v <= d_v in lex order;
- *  - evaluation grid: G = prod_v N_v nodes, N_v = nextpow2(D_v + 1),
- *    D_v = n * d_v; node (i1..ik) is x_v = w_v^(i_v) with w_v = g^((p-1)/N_v)
- *    for the least generator g of (Z/pZ)^*, flat index lex (i1 slowest);
+ *  - evaluation nodes: G = prod_v M_v nodes, node (i1..ik) is
+ *    x_v = w_v^(i_v), 0 <= i_v < M_v, with w_v = g^((p-1)/N_v) for the least
+ *    generator g of (Z/pZ)^*, N_v = nextpow2(D_v + 1), D_v = n * d_v, and
+ *    M_v = D_v + 1 (node grid, default) or N_v (POLYDET_FLAG_FULL_GRID);
+ *    flat index lex (i1 slowest);
  *  - determinant coefficients: C = prod_v (D_v + 1), lex over e_v <= D_v.
  */
 #ifndef POLYDET_H
@@ -75,7 +77,18 @@ typedef struct polydet_plan_info {
   int32_t N[POLYDET_MAX_VARS];     /* grid size per variable               */
   uint64_t eval_ws_words;          /* polydet_eval scratch per prime       */
   uint64_t interp_ws_words;        /* polydet_interp scratch per prime     */
+  int32_t M[POLYDET_MAX_VARS];     /* evaluation nodes per variable        */
+  uint32_t flags;                  /* the plan's flags                     */
 } polydet_plan_info;
+
+/* Plan flag: evaluate on the full power-of-two grid (N_v nodes per variable)
+ * and interpolate by inverse NTT, as the paper does (Sec. 3.1, 3.3).  Without
+ * it the plan evaluates on the node grid: the first D_v + 1 powers of w_v,
+ * i.e. exactly as many nodes as the degree bound needs (Sec. 2), and
+ * interpolates with the inverse of their Vandermonde matrix.  Both give the
+ * same determinant; the node grid condenses prod (D_v+1) / prod N_v as many
+ * matrices. */
+#define POLYDET_FLAG_FULL_GRID 0x1u
 
 /* Primes of Eq. 1 with q = 20: every p = c * 2^20 + 1 in (2^30, 2^31), largest
  * first.  Returns the table size (91) when `out` is NULL, else writes that
@@ -97,7 +110,8 @@ int polydet_hadamard_primes(int n, const int64_t *entry_l1, int *nprimes_out,
  * primes of the table (must be >= 1).  Allocates the plan's small device
  * tables (Montgomery constants, twiddles, Garner tables, status word); no
  * later call allocates device memory: scratch is passed in by the caller.
- * `flags` must be 0.  The plan must be destroyed with polydet_plan_destroy. */
+ * `flags` is 0 or POLYDET_FLAG_FULL_GRID.  The plan must be destroyed with
+ * polydet_plan_destroy. */
 int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
                  int nprimes, uint32_t flags);
 int polydet_plan_destroy(polydet_plan_t plan);
@@ -124,9 +138,10 @@ int polydet_condense_batch(polydet_plan_t plan, const uint32_t *evals_dev,
                            int prime_lo, int prime_hi, uint32_t *detvals_dev,
                            void *stream);
 
-/* Stage 3, interpolation (Sec. 3.3): inverse NTT with the 1/N factor,
- * keeping the C coefficients with e_v <= D_v.  Any nonzero coefficient with
- * e_v > D_v sets POLYDET_STATUS_BOUND.  detvals_dev: device uint32
+/* Stage 3, interpolation (Sec. 3.3): on the full grid the inverse NTT with the
+ * 1/N factor, keeping the C coefficients with e_v <= D_v (any nonzero
+ * coefficient with e_v > D_v sets POLYDET_STATUS_BOUND); on the node grid the
+ * inverse Vandermonde matrix of the nodes, one variable at a time.  detvals_dev: device uint32
  * [prime_hi - prime_lo][G] (read only); residues_dev: device uint32
  * [prime_hi - prime_lo][C]; ws_dev: device scratch of
  * (prime_hi - prime_lo) * info.interp_ws_words words (NULL allowed when 0).
@@ -201,6 +216,7 @@ typedef struct polydet_job {
   int32_t nvars;               /* variables, 1..POLYDET_MAX_VARS          */
   int32_t nprimes;             /* primes (polydet_hadamard_primes)        */
   int32_t d[POLYDET_MAX_VARS]; /* entry degree bound per variable         */
+  uint32_t flags;              /* 0 or POLYDET_FLAG_FULL_GRID             */
 } polydet_job;
 
 typedef struct polydet_batch_s *polydet_batch_t;

@@ -174,6 +174,47 @@ def interp_grid(values: Sequence[int], Ns: Sequence[int], omegas: Sequence[int],
     return box, clean
 
 
+def solve_mod_p(A: Sequence[Sequence[int]], b: Sequence[int], p: int) -> List[int]:
+    """x with A x = b over F_p (A square, invertible): Gauss-Jordan."""
+    n = len(A)
+    M = [[int(v) % p for v in row] + [int(bb) % p] for row, bb in zip(A, b)]
+    for c in range(n):
+        r = next(i for i in range(c, n) if M[i][c])
+        M[c], M[r] = M[r], M[c]
+        inv = pow(M[c][c], p - 2, p)
+        M[c] = [v * inv % p for v in M[c]]
+        for i in range(n):
+            if i != c and M[i][c]:
+                f = M[i][c]
+                M[i] = [(vi - f * vc) % p for vi, vc in zip(M[i], M[c])]
+    return [M[i][n] for i in range(n)]
+
+
+def interp_nodes(values: Sequence[int], Ms: Sequence[int], omegas: Sequence[int],
+                 p: int) -> List[int]:
+    """Interpolation through the node grid x_v = omega_v^i, 0 <= i < M_v
+    (Sec. 3.3: unique polynomial of degree < M_v in each variable through
+    those nodes): one Vandermonde system V c = y per line, variable by
+    variable.  ``values`` lex over the grid; returns lex coefficients of the
+    box prod [0, M_v)."""
+    k = len(Ms)
+    cur = [int(v) % p for v in values]
+    for v in range(k - 1, -1, -1):
+        m = Ms[v]
+        V = [[pow(omegas[v], i * e, p) for e in range(m)] for i in range(m)]
+        inner = prod(Ms[v + 1:])
+        outer = prod(Ms[:v])
+        nxt = [0] * len(cur)
+        for a in range(outer):
+            for b in range(inner):
+                idx = [(a * m + i) * inner + b for i in range(m)]
+                coef = solve_mod_p(V, [cur[t] for t in idx], p)
+                for e, t in enumerate(idx):
+                    nxt[t] = coef[e]
+        cur = nxt
+    return cur
+
+
 def mixed_radix_digits(xs: Sequence[int], primes: Sequence[int]) -> List[int]:
     """Garner / MRC digits (Sec. 3.4, reading of Eq. for alpha_i):
     X = sum_i alpha_i prod_{l<i} p_l with 0 <= alpha_i < p_i and

@@ -37,16 +37,20 @@ class PlanInfo(ctypes.Structure):
                 ("W", ctypes.c_int32), ("E", ctypes.c_int64), ("G", ctypes.c_int64),
                 ("C", ctypes.c_int64), ("d", ctypes.c_int32 * MAX_VARS),
                 ("D", ctypes.c_int32 * MAX_VARS), ("N", ctypes.c_int32 * MAX_VARS),
-                ("eval_ws_words", ctypes.c_uint64), ("interp_ws_words", ctypes.c_uint64)]
+                ("eval_ws_words", ctypes.c_uint64), ("interp_ws_words", ctypes.c_uint64),
+                ("M", ctypes.c_int32 * MAX_VARS), ("flags", ctypes.c_uint32)]
 
 
 MAX_N = 32
 OFF_COEFFS, OFF_PARTIAL, OFF_DETVALS, OFF_RESIDUES, OFF_LIMBS = 0, 1, 2, 3, 4
 
 
+FLAG_FULL_GRID = 0x1
+
+
 class Job(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nvars", ctypes.c_int32), ("nprimes", ctypes.c_int32),
-                ("d", ctypes.c_int32 * MAX_VARS)]
+                ("d", ctypes.c_int32 * MAX_VARS), ("flags", ctypes.c_uint32)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -166,13 +170,15 @@ def _stream(stream: Optional[torch.cuda.Stream]) -> ctypes.c_void_p:
 
 class Plan:
     """A polydet plan: n x n matrices in len(degs) variables, entry degree
-    <= degs[v] in x_v, over the first ``nprimes`` primes of the table."""
+    <= degs[v] in x_v, over the first ``nprimes`` primes of the table; node
+    grid (default) or the paper's full power-of-two grid."""
 
-    def __init__(self, n: int, degs: Sequence[int], nprimes: int):
+    def __init__(self, n: int, degs: Sequence[int], nprimes: int, full_grid: bool = False):
         L = lib()
         d = (ctypes.c_int32 * len(degs))(*[int(x) for x in degs])
         h = ctypes.c_void_p()
-        _check(L.polydet_plan(ctypes.byref(h), int(n), len(degs), d, int(nprimes), 0), "polydet_plan")
+        _check(L.polydet_plan(ctypes.byref(h), int(n), len(degs), d, int(nprimes),
+                              FLAG_FULL_GRID if full_grid else 0), "polydet_plan")
         self._h = h
         info = PlanInfo()
         _check(L.polydet_plan_query(h, ctypes.byref(info)), "polydet_plan_query")
@@ -181,6 +187,8 @@ class Plan:
         self.d = tuple(info.d[:self.k])
         self.D = tuple(info.D[:self.k])
         self.N = tuple(info.N[:self.k])
+        self.M = tuple(info.M[:self.k])  # evaluation nodes per variable
+        self.full_grid = bool(info.flags & FLAG_FULL_GRID)
         self.eval_ws_words = int(info.eval_ws_words)
         self.interp_ws_words = int(info.interp_ws_words)
         pr = (ctypes.c_uint32 * self.P)()
@@ -269,11 +277,12 @@ class Batch:
     """A polydet batch: jobs of any shape, one fused run for all of them.
     ``jobs`` is a list of (n, degs, nprimes)."""
 
-    def __init__(self, jobs: Sequence[tuple]):
+    def __init__(self, jobs: Sequence[tuple], full_grid: bool = False):
         L = lib()
         arr = (Job * len(jobs))()
         for i, (n, degs, P) in enumerate(jobs):
             arr[i].n, arr[i].nvars, arr[i].nprimes = int(n), len(degs), int(P)
+            arr[i].flags = FLAG_FULL_GRID if full_grid else 0
             for v, dv in enumerate(degs):
                 arr[i].d[v] = int(dv)
         h = ctypes.c_void_p()

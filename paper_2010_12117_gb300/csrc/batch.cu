@@ -59,12 +59,10 @@ static int build_class(polydet_batch_s *b, int n) {
     it += (s.G + S - 1) / S;
   }
   b->nitems[n] = it;
-  // shared memory for the partial-tensor rows of one item: S / N_k rows (items
-  // are S-aligned and S, N_k are powers of two) or one
+  // shared memory for the partial-tensor rows one item can span
   size_t qw = 0;
-  for (const auto &s : v) {
-    const int64_t Nk = (int64_t)1 << s.logNk;
-    const int64_t rows = S > Nk ? S / Nk : 1;
+  for (const auto &s : v) {  // an item of S nodes spans at most ceil(S / M_k) + 1 rows
+    const int64_t rows = std::min<int64_t>((S + s.Mk - 1) / s.Mk + 1, (s.G + s.Mk - 1) / s.Mk);
     qw = std::max<size_t>(qw, (size_t)rows * n * n * s.Lp);
   }
   b->qwords[n] = qw;
@@ -102,7 +100,7 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
       return POLYDET_EINVAL;
     }
     polydet_plan_t pl = nullptr;
-    int rc = polydet_plan(&pl, jb.n, jb.nvars, jb.d, jb.nprimes, 0);
+    int rc = polydet_plan(&pl, jb.n, jb.nvars, jb.d, jb.nprimes, jb.flags);
     if (rc) {
       destroy_batch(b);
       return rc;
@@ -113,7 +111,7 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
     const int Lp = pow2_at_least(L);
     b->Lp.push_back(Lp);
     const int64_t n2 = (int64_t)pl->n * pl->n;
-    const int64_t rows = pl->G / pl->N[k - 1];
+    const int64_t rows = pl->G / pl->M[k - 1];
     const int64_t part = ((int64_t)pl->P * rows * n2 * Lp + 7) / 8 * 8;
     b->coeff_off.push_back(b->coeff_off.back() + n2 * pl->E);
     b->part_off.push_back(b->part_off.back() + part);
@@ -129,7 +127,7 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
     polydet_plan_s *pl = b->plans[j];
     const int k = pl->nvars;
     const int64_t n2 = (int64_t)pl->n * pl->n;
-    const int64_t rows = pl->G / pl->N[k - 1];
+    const int64_t rows = pl->G / pl->M[k - 1];
     for (int q = 0; q < pl->P; ++q) {
       FusedSeg s = {};
       s.G = pl->G;
@@ -139,6 +137,7 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
       s.md = pl->mod_h[q];
       s.rn = pl->rn_h[q];
       s.logNk = pl->logN[k - 1];
+      s.Mk = pl->M[k - 1];
       s.L = pl->d[k - 1] + 1;
       s.Lp = b->Lp[j];
       b->segs[pl->n].push_back(s);

@@ -102,6 +102,13 @@ struct polydet_plan_s {
   int n, nvars, P, W;
   int64_t E, G, C;
   int d[POLYDET_MAX_VARS], D[POLYDET_MAX_VARS], N[POLYDET_MAX_VARS], logN[POLYDET_MAX_VARS];
+  // nodes per variable: D_v + 1 (node grid: the first D_v + 1 powers of w_v)
+  // or N_v (full grid, POLYDET_FLAG_FULL_GRID); G = prod_v M_v
+  int M[POLYDET_MAX_VARS];
+  int full;                        // 1: full power-of-two grid + inverse NTT
+  int vinv_off[POLYDET_MAX_VARS];  // node grid: offset of variable v's table
+  int vinv_len;                    // node grid: sum_v M_v^2 words per prime
+  uint32_t *d_vinv;                // [P][vinv_len] inverse Vandermonde * R
   int tw_len;                      // sum_v N_v / 2: twiddles per prime
   uint32_t primes[POLYDET_MAX_PRIMES];
   uint32_t roots[POLYDET_MAX_PRIMES][POLYDET_MAX_VARS];
@@ -139,7 +146,7 @@ int pd_launch_condense(const polydet_plan_s *pl, const uint32_t *evals, int prim
                        int nprimes, uint32_t *detvals, cudaStream_t st);
 
 // Evaluation of every variable but the last (x_k), for the fused kernels:
-// out[q][row][entry][Lp] with row over prod_{v<k} N_v (lex) holding the
+// out[q][row][entry][Lp] with row over prod_{v<k} M_v (lex) holding the
 // coefficients of x_k^l, l < L = d_k + 1 (Lp >= L, padding unwritten).
 // Needs pd_partial_ws_words(pl) * (hi - lo) words of scratch.
 int pd_eval_partial(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int hi,
@@ -156,7 +163,8 @@ struct FusedSeg {
   const uint32_t *tw;  // w_k^j * R for j < N_k / 2 (last variable, this prime)
   ModP md;
   uint32_t rn;         // R^n mod p
-  int32_t logNk;       // log2 N_k
+  int32_t logNk;       // log2 N_k (twiddle table of the last variable)
+  int32_t Mk;          // nodes of the last variable (M_k): node g = row * Mk + i
   int32_t L, Lp;       // coefficients of x_k per entry, stride of the partial tensor
 };
 

@@ -1,9 +1,10 @@
 // Determinant mod p of one n x n matrix per grid node (Sec. 3.2, Algorithm 3).
 //
 // A team of T consecutive lanes owns one matrix: lane t holds the columns
-// j = t, t + T, t + 2T, ... entirely in registers (n <= 12: one lane per
-// matrix; up to 32: 2, 4 or 8 lanes).  Every index into the register array
-// is a compile-time constant after unrolling, so nothing spills to local
+// j = t, t + T, t + 2T, ... entirely in registers (one lane for n <= 8; 2,
+// 4, 8 or 16 lanes up to n = 32).  Every index into the register array
+// is a compile-time constant after unrolling (see TeamFor for the lanes per
+// matrix of each order), so nothing spills to local
 // memory, and there are no barriers: the team talks through warp shuffles.
 //
 // Elimination is fraction free (the paper's update, Algorithm 3 step (3)):
@@ -120,7 +121,9 @@ __global__ void __launch_bounds__(128) condense_kernel(const uint32_t *__restric
 
 template <int NN>
 struct TeamFor {
-  static constexpr int value = NN <= 12 ? 1 : (NN <= 16 ? 2 : (NN <= 20 ? 4 : 8));
+  // lanes per determinant: keeps the register-resident matrix near 64
+  // words per lane so that four CTAs of 128 threads fit on an SM
+  static constexpr int value = NN <= 8 ? 1 : (NN <= 11 ? 2 : (NN <= 16 ? 4 : (NN <= 24 ? 8 : 16)));
 };
 
 template <int NN, int HI>

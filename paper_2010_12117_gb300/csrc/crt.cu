@@ -71,9 +71,99 @@ __global__ void __launch_bounds__(128) crt_kernel(const uint32_t *__restrict__ r
   }
 }
 
+// The same computation with the prime count a compile-time constant (P <= 32,
+// so W <= P): digits, limbs and the Horner carries stay in registers, the
+// Garner table and the constants sit in shared memory, and a grid-stride
+// loop covers the coefficients.
+template <int PT>
+__global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__ res,
+                                                    uint32_t *__restrict__ limbs, int64_t C, int W,
+                                                    const ModP *__restrict__ mod,
+                                                    const uint32_t *__restrict__ garner,
+                                                    const uint32_t *__restrict__ mhalf,
+                                                    const uint32_t *__restrict__ mfull) {
+  __shared__ uint32_t gs[PT * PT];
+  __shared__ uint32_t ps[PT], pis[PT], mh[PT], mf[PT];
+  for (int i = threadIdx.x; i < PT * PT; i += blockDim.x) gs[i] = garner[i];
+  for (int i = threadIdx.x; i < PT; i += blockDim.x) {
+    ps[i] = mod[i].p;
+    pis[i] = mod[i].pinv;
+    mh[i] = i < W ? mhalf[i] : 0u;
+    mf[i] = i < W ? mfull[i] : 0u;
+  }
+  __syncthreads();
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t x[PT], al[PT];
+#pragma unroll
+    for (int i = 0; i < PT; ++i) x[i] = __ldg(res + (int64_t)i * C + c);
+    al[0] = x[0];
+#pragma unroll
+    for (int i = 1; i < PT; ++i) {
+      const uint32_t p = ps[i], pinv = pis[i];
+      uint32_t acc = 0u;
+#pragma unroll
+      for (int j = 0; j < i; ++j) acc = addm(acc, mmul(al[j], gs[i * PT + j], p, pinv), p);
+      al[i] = mmul(subm(x[i], acc, p), gs[i * PT + i], p, pinv);
+    }
+    uint32_t X[PT];
+#pragma unroll
+    for (int w = 0; w < PT; ++w) X[w] = 0u;
+    X[0] = al[PT - 1];
+#pragma unroll
+    for (int i = PT - 2; i >= 0; --i) {
+      uint64_t carry = al[i];
+      const uint32_t pi = ps[i];
+#pragma unroll
+      for (int w = 0; w < PT - i; ++w) {
+        const uint64_t t = (uint64_t)X[w] * pi + carry;
+        X[w] = (uint32_t)t;
+        carry = t >> 32;
+      }
+    }
+    int cmp = 0;
+#pragma unroll
+    for (int w = PT - 1; w >= 0; --w)
+      if (cmp == 0 && w < W) cmp = (X[w] > mh[w]) ? 1 : ((X[w] < mh[w]) ? -1 : 0);
+    if (cmp > 0) {
+      uint32_t borrow = 0u;
+#pragma unroll
+      for (int w = 0; w < PT; ++w) {
+        const uint64_t t = (uint64_t)X[w] - mf[w] - borrow;
+        X[w] = (uint32_t)t;
+        borrow = (uint32_t)(t >> 63);
+      }
+    }
+    uint32_t *o = limbs + c * W;
+#pragma unroll
+    for (int w = 0; w < PT; ++w)
+      if (w < W) o[w] = X[w];
+  }
+}
+
+template <int PT>
+static int launch_crt_p(const polydet_plan_s *pl, const uint32_t *residues, uint32_t *limbs,
+                        cudaStream_t st) {
+  if (pl->P == PT) {
+    int dev = 0, sms = 0;
+    PD_CUDA(cudaGetDevice(&dev));
+    PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256;
+    const int64_t want = (pl->C + threads - 1) / threads;
+    const unsigned blocks = (unsigned)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
+    crt_kernel_p<PT><<<blocks, threads, 0, st>>>(residues, limbs, pl->C, pl->W, pl->d_mod,
+                                                 pl->d_garner, pl->d_mhalf, pl->d_mfull);
+    PD_CUDA(cudaGetLastError());
+    return POLYDET_OK;
+  }
+  if constexpr (PT < 32) return launch_crt_p<PT + 1>(pl, residues, limbs, st);
+  return POLYDET_EINVAL;
+}
+
 extern "C" int polydet_crt(polydet_plan_t pl, const uint32_t *residues, uint32_t *limbs,
                            void *stream) {
   if (!pl || !residues || !limbs) return POLYDET_EINVAL;
+  if (pl->P <= 32 && pl->W <= pl->P) return launch_crt_p<1>(pl, residues, limbs, (cudaStream_t)stream);
   const int threads = 128;
   const size_t smem = (size_t)(pl->P + pl->W) * threads * sizeof(uint32_t);
   static bool attr_set = false;

@@ -78,4 +78,4 @@ int pd_fused_occupancy(int n, int threads, size_t qwords, int *bps) {
   return POLYDET_EINVAL;
 }
 
-int pd_fused_team(int n) { return n <= 12 ? 1 : (n <= 16 ? 2 : (n <= 20 ? 4 : 8)); }
+int pd_fused_team(int n) { return n <= 8 ? 1 : (n <= 11 ? 2 : (n <= 16 ? 4 : (n <= 24 ? 8 : 16))); }

@@ -14,7 +14,7 @@
 // in global memory until the list is exhausted, so one launch covers every
 // (job, prime) pair of a matrix order, whatever the mix of grid sizes.  Per
 // item:
-//  0. the CTA copies the Q rows its nodes need (S / N_k rows, or one) into
+//  0. the CTA copies the Q rows its nodes need (about S / M_k + 1) into
 //     shared memory with coalesced 16-byte loads;
 //  1. a team of T lanes owns node g = (row, i): it forms x = w_k^i
 //     (Montgomery form, from the twiddle table) and its powers, and evaluates
@@ -148,11 +148,12 @@ __global__ void __launch_bounds__(128) fused_kernel(const FusedSeg *__restrict__
     const FusedSeg &sg = segs[si];
     const uint32_t p = sg.md.p, pinv = sg.md.pinv;
     const int logNk = sg.logNk;
+    const int64_t Mk = sg.Mk;
     const int Lp = sg.Lp;
     const int64_t g0 = (item - sg.item0) * S;
-    const int64_t row0 = g0 >> logNk;
+    const int64_t row0 = g0 / Mk;
     const int64_t glast = min(g0 + S, sg.G) - 1;
-    const int nrows = (int)((glast >> logNk) - row0 + 1);
+    const int nrows = (int)(glast / Mk - row0 + 1);
 
     // 0. this item's Q rows into shared memory (contiguous in global memory)
     {
@@ -171,7 +172,8 @@ __global__ void __launch_bounds__(128) fused_kernel(const FusedSeg *__restrict__
     const int64_t g = g0 + team;
     const bool active = g < sg.G;
     const int64_t gg = active ? g : glast;
-    const int ik = (int)(gg & ((1 << logNk) - 1));
+    const int64_t grow = gg / Mk;
+    const int ik = (int)(gg - grow * Mk);
     const int L = sg.L;
     uint32_t X[8];
     X[0] = sg.md.r1;
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(128) fused_kernel(const FusedSeg *__restrict__
 
     // 1. entries of this lane's columns at its node, into its slice
     uint32_t *mine = ent + threadIdx.x;
-    fused_eval_entries<NN, T>(qsm + ((gg >> logNk) - row0) * NN2 * Lp, t, X, L, Lp, p, pinv, mine,
+    fused_eval_entries<NN, T>(qsm + (grow - row0) * NN2 * Lp, t, X, L, Lp, p, pinv, mine,
                               bd);
     // 2. elimination in registers
     fused_det<NN, T>(mine, bd, t, sg.md, sg.rn, active && t == 0, detvals + sg.det_off + g);

@@ -125,6 +125,115 @@ __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
   if (bad) atomicOr(a.status, POLYDET_STATUS_BOUND);
 }
 
+// Forward pass for short inputs (Lin <= LP <= 8): one thread per column,
+// no shared memory.  The N outputs y_i = sum_{e<Lin} c_e w^(i e) are produced
+// coset by coset: for i = j + (N/LP) t, y = DFT_LP(c_e w^(j e))[t] with the
+// LP-th root psi = w^(N/LP), i.e. LP - 1 twiddles and a register DFT of
+// size LP per LP outputs (1 mulmod per output for LP = 4, 1.5 for LP = 8).
+// Consecutive threads hold consecutive columns, so every store of a row is
+// coalesced.
+__device__ __forceinline__ uint32_t tw_pow(const uint32_t *tw, int k, int N, uint32_t p) {
+  const int h = N >> 1;  // w^(k) for 0 <= k < N from the table of w^j, j < N/2
+  return k < h ? __ldg(tw + k) : p - __ldg(tw + (k - h));
+}
+
+template <int LP>
+__global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
+  const int q = a.prime_lo + blockIdx.z;
+  const ModP md = a.mod[q];
+  const uint32_t p = md.p, pinv = md.pinv;
+  const int64_t ncols = a.A * a.B;
+  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncols) return;
+  const int64_t aa = col / a.B, bb = col - aa * a.B;
+  const int64_t in_base = (int64_t)blockIdx.z * a.in_prime_stride + (int64_t)blockIdx.y * a.in_item_stride;
+  uint32_t c[LP];
+#pragma unroll
+  for (int e = 0; e < LP; ++e) {
+    uint32_t v = 0u;
+    if (e < a.Lin) {
+      const int64_t idx = in_base + (aa * a.Lin + e) * a.B + bb;
+      v = a.in_is_i32 ? reduce_i32(((const int32_t *)a.in)[idx], p) : ((const uint32_t *)a.in)[idx];
+    }
+    c[e] = v;
+  }
+  const int N = a.N;
+  const uint32_t *tw = a.tw + (size_t)q * a.tw_len + a.tw_off;
+  // output address of row i of this column
+  int64_t obase, ostride;
+  if (a.il_L) {
+    const int64_t rowrest = bb / a.il_L;
+    obase = (int64_t)blockIdx.z * a.out_prime_stride + (rowrest * a.il_n2 + blockIdx.y) * a.il_Lp + bb % a.il_L;
+    ostride = (a.B / a.il_L) * a.il_n2 * a.il_Lp;  // row r -> row index r * (B / L)
+  } else {
+    obase = (int64_t)blockIdx.z * a.out_prime_stride + (int64_t)blockIdx.y * a.out_item_stride +
+            aa * a.Lout * a.B + bb;
+    ostride = a.B;
+  }
+  uint32_t *out = a.out;
+  const int J = N / LP;
+  uint32_t r4 = 0u, psi1 = 0u, psi2 = 0u, psi3 = 0u;
+  if (LP >= 4) r4 = __ldg(tw + (N >> 2));  // w^(N/4), a primitive 4th root
+  if (LP == 8) {
+    psi1 = __ldg(tw + (N >> 3));
+    psi2 = r4;
+    psi3 = __ldg(tw + 3 * (N >> 3));
+  }
+  for (int j = 0; j < J; ++j) {
+    uint32_t z[LP];
+    z[0] = c[0];
+#pragma unroll
+    for (int e = 1; e < LP; ++e) z[e] = (e < a.Lin) ? mmul(tw_pow(tw, j * e, N, p), c[e], p, pinv) : 0u;
+    uint32_t y[LP];
+    if (LP == 1) {
+      y[0] = z[0];
+    } else if (LP == 2) {
+      y[0] = addm(z[0], z[1], p);
+      y[1] = subm(z[0], z[1], p);
+    } else {
+      // DFT_4 of (z0, z2, z4, z6) [LP = 8] or (z0, z1, z2, z3) [LP = 4]
+      const int s = LP / 4;
+      uint32_t E[4];
+      {
+        const uint32_t a0 = addm(z[0], z[2 * s], p), a1 = subm(z[0], z[2 * s], p);
+        const uint32_t b0 = addm(z[s], z[3 * s], p);
+        const uint32_t b1 = mmul(r4, subm(z[s], z[3 * s], p), p, pinv);
+        E[0] = addm(a0, b0, p);
+        E[2] = subm(a0, b0, p);
+        E[1] = addm(a1, b1, p);
+        E[3] = subm(a1, b1, p);
+      }
+      if (LP == 4) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) y[t] = E[t];
+      } else {
+        uint32_t O[4];
+        const uint32_t a0 = addm(z[1], z[5], p), a1 = subm(z[1], z[5], p);
+        const uint32_t b0 = addm(z[3], z[7], p);
+        const uint32_t b1 = mmul(r4, subm(z[3], z[7], p), p, pinv);
+        O[0] = addm(a0, b0, p);
+        O[2] = subm(a0, b0, p);
+        O[1] = addm(a1, b1, p);
+        O[3] = subm(a1, b1, p);
+        const uint32_t t1 = mmul(psi1, O[1], p, pinv);
+        const uint32_t t2 = mmul(psi2, O[2], p, pinv);
+        const uint32_t t3 = mmul(psi3, O[3], p, pinv);
+        y[0] = addm(E[0], O[0], p);
+        y[4] = subm(E[0], O[0], p);
+        y[1] = addm(E[1], t1, p);
+        y[5] = subm(E[1], t1, p);
+        y[2] = addm(E[2], t2, p);
+        y[6] = subm(E[2], t2, p);
+        y[3] = addm(E[3], t3, p);
+        y[7] = subm(E[3], t3, p);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < LP; ++t)
+      if (j + J * t < a.Lout) out[obase + (int64_t)(j + J * t) * ostride] = y[t];
+  }
+}
+
 static int ilog2(int64_t x) {
   int l = 0;
   while (((int64_t)1 << l) < x) ++l;
@@ -132,8 +241,21 @@ static int ilog2(int64_t x) {
 }
 
 static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
-  // Ct: columns per CTA, a power of two with N * (Ct + 1) words <= 64 KB.
   int64_t ncols = a.A * a.B;
+  // short forward transforms over many columns: the register-direct kernel
+  if (!a.inverse && a.Lin <= 8 && a.B >= 8) {
+    const int LP = a.Lin <= 1 ? 1 : a.Lin <= 2 ? 2 : a.Lin <= 4 ? 4 : 8;
+    dim3 grid((unsigned)((ncols + 255) / 256), (unsigned)items, (unsigned)nprimes);
+    switch (LP) {
+      case 1: coltx_direct_kernel<1><<<grid, 256, 0, st>>>(a); break;
+      case 2: coltx_direct_kernel<2><<<grid, 256, 0, st>>>(a); break;
+      case 4: coltx_direct_kernel<4><<<grid, 256, 0, st>>>(a); break;
+      default: coltx_direct_kernel<8><<<grid, 256, 0, st>>>(a); break;
+    }
+    PD_CUDA(cudaGetLastError());
+    return POLYDET_OK;
+  }
+  // Ct: columns per CTA, a power of two with N * (Ct + 1) words <= 64 KB.
   int ct = 32;
   while (ct > 1 && (int64_t)a.N * (ct + 1) > 16384) ct >>= 1;
   while (ct > 1 && ct / 2 >= ncols) ct >>= 1;
@@ -171,11 +293,11 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
     a.A = 1;
     for (int u = 0; u < v; ++u) a.A *= pl->d[u] + 1;
     a.B = 1;
-    for (int u = v + 1; u < k; ++u) a.B *= pl->N[u];
+    for (int u = v + 1; u < k; ++u) a.B *= pl->M[u];
     a.Lin = pl->d[v] + 1;
     a.N = pl->N[v];
     a.logN = pl->logN[v];
-    a.Lout = a.N;
+    a.Lout = pl->M[v];  // the first M_v outputs of the N_v-point transform
     a.in = cur_in;
     a.in_item_stride = cur_item;
     a.in_prime_stride = cur_prime;
@@ -208,11 +330,116 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
   return POLYDET_OK;
 }
 
+// Node-grid interpolation of one variable: every column (a, b) of the tensor
+// [A][m][B] holds the values at the nodes w^0..w^(m-1) of a polynomial of
+// degree < m in that variable; its coefficients are V^-1 y (V the Vandermonde
+// matrix of the nodes, its inverse in Montgomery form in `vinv`).  A CTA
+// stages Ct columns x m values in shared memory; each thread then forms
+// output coefficients as dot products with rows of V^-1, read by every lane
+// of a warp at the same address (broadcast).
+struct VmArgs {
+  const uint32_t *in;
+  uint32_t *out;
+  int64_t in_prime_stride, out_prime_stride;
+  int64_t A, B;
+  int m, Ct;
+  int prime_lo;
+  const ModP *mod;
+  const uint32_t *vinv;  // this variable's table for prime 0
+  int vinv_len;          // words per prime
+};
+
+__global__ void __launch_bounds__(256) vmat_kernel(VmArgs a) {
+  extern __shared__ uint32_t sm[];
+  const int q = a.prime_lo + blockIdx.z;
+  const ModP md = a.mod[q];
+  const int m = a.m, Ct = a.Ct, S = Ct + 1;
+  const int64_t ncols = a.A * a.B;
+  const int64_t col0 = (int64_t)blockIdx.x * Ct;
+  const uint32_t *in = a.in + (int64_t)blockIdx.z * a.in_prime_stride;
+  uint32_t *out = a.out + (int64_t)blockIdx.z * a.out_prime_stride;
+  for (int f = threadIdx.x; f < m * Ct; f += blockDim.x) {
+    const int r = f / Ct, c = f - r * Ct;
+    const int64_t col = col0 + c;
+    uint32_t v = 0u;
+    if (col < ncols) {
+      const int64_t aa = col / a.B, bb = col - aa * a.B;
+      v = in[(aa * m + r) * a.B + bb];
+    }
+    sm[r * S + c] = v;
+  }
+  __syncthreads();
+  const uint32_t *V = a.vinv + (size_t)q * a.vinv_len;
+  for (int f = threadIdx.x; f < m * Ct; f += blockDim.x) {
+    const int e = f / Ct, c = f - e * Ct;
+    const int64_t col = col0 + c;
+    if (col >= ncols) continue;
+    const uint32_t *row = V + (size_t)e * m;
+    uint32_t acc = 0u;
+    int i = 0;
+    for (; i + 1 < m; i += 2) {  // two products per REDC: 2 p^2 < p 2^32
+      const uint64_t s2 = (uint64_t)__ldg(row + i) * sm[i * S + c] +
+                          (uint64_t)__ldg(row + i + 1) * sm[(i + 1) * S + c];
+      acc = addm(acc, redc(s2, md.p, md.pinv), md.p);
+    }
+    if (i < m) acc = addm(acc, mmul(__ldg(row + i), sm[i * S + c], md.p, md.pinv), md.p);
+    const int64_t aa = col / a.B, bb = col - aa * a.B;
+    out[(aa * m + e) * a.B + bb] = acc;
+  }
+}
+
+static int interp_nodes(polydet_plan_t pl, const uint32_t *detvals, int lo, int hi,
+                        uint32_t *residues, uint32_t *ws, cudaStream_t st) {
+  const int k = pl->nvars, np = hi - lo;
+  const uint64_t slot = pl->interp_ws_words / 2;
+  static bool attr_set = false;
+  if (!attr_set) {
+    PD_CUDA(cudaFuncSetAttribute(vmat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  const uint32_t *cur = detvals;
+  int64_t cur_prime = pl->G;
+  int t = 0;
+  for (int v = k - 1; v >= 0; --v, ++t) {
+    VmArgs a = {};
+    a.A = 1;
+    for (int u = 0; u < v; ++u) a.A *= pl->M[u];
+    a.B = 1;
+    for (int u = v + 1; u < k; ++u) a.B *= pl->M[u];
+    a.m = pl->M[v];
+    int ct = 32;
+    while (ct > 1 && (int64_t)a.m * (ct + 1) > 16384) ct >>= 1;
+    while (ct > 1 && ct / 2 >= a.A * a.B) ct >>= 1;
+    a.Ct = ct;
+    a.in = cur;
+    a.in_prime_stride = cur_prime;
+    if (v == 0) {
+      a.out = residues;
+      a.out_prime_stride = pl->C;
+    } else {
+      a.out = ws + (uint64_t)(t % 2) * slot * (uint64_t)np;
+      a.out_prime_stride = (int64_t)slot;
+    }
+    a.prime_lo = lo;
+    a.mod = pl->d_mod;
+    a.vinv = pl->d_vinv + pl->vinv_off[v];
+    a.vinv_len = pl->vinv_len;
+    const size_t smem = (size_t)a.m * (ct + 1) * sizeof(uint32_t);
+    dim3 grid((unsigned)((a.A * a.B + ct - 1) / ct), 1, (unsigned)np);
+    vmat_kernel<<<grid, 256, smem, st>>>(a);
+    PD_CUDA(cudaGetLastError());
+    cur = a.out;
+    cur_prime = a.out_prime_stride;
+  }
+  return POLYDET_OK;
+}
+
 extern "C" int polydet_interp(polydet_plan_t pl, const uint32_t *detvals, int lo, int hi,
                               uint32_t *residues, uint32_t *ws, void *stream) {
   if (check_range(pl, lo, hi) || !detvals || !residues) return POLYDET_EINVAL;
   if (pl->interp_ws_words && !ws) return POLYDET_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (!pl->full) return interp_nodes(pl, detvals, lo, hi, residues, ws, st);
   const int k = pl->nvars, np = hi - lo;
   const uint64_t slot = pl->interp_ws_words / 2;
   const void *cur_in = detvals;
@@ -264,7 +491,7 @@ uint64_t pd_partial_ws_words(const polydet_plan_s *pl) {
   uint64_t best = 0;
   for (int v = 1; v <= k - 2; ++v) {
     uint64_t s = (uint64_t)(pl->d[k - 1] + 1);
-    for (int u = 0; u < k - 1; ++u) s *= (u < v) ? (uint64_t)(pl->d[u] + 1) : (uint64_t)pl->N[u];
+    for (int u = 0; u < k - 1; ++u) s *= (u < v) ? (uint64_t)(pl->d[u] + 1) : (uint64_t)pl->M[u];
     if (s > best) best = s;
   }
   return 2 * best * (uint64_t)pl->n * pl->n;
@@ -277,7 +504,7 @@ int pd_eval_partial(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int
   const int64_t n2 = (int64_t)pl->n * pl->n;
   const int Lk = pl->d[k - 1] + 1;
   int64_t rows = 1;
-  for (int u = 0; u < k - 1; ++u) rows *= pl->N[u];
+  for (int u = 0; u < k - 1; ++u) rows *= pl->M[u];
   const uint64_t slot = pd_partial_ws_words(pl) / (2 * (uint64_t)n2);
   const void *cur_in = coeffs;
   int64_t cur_item = pl->E, cur_prime = 0;
@@ -288,11 +515,11 @@ int pd_eval_partial(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int
     a.A = 1;
     for (int u = 0; u < v; ++u) a.A *= pl->d[u] + 1;
     a.B = Lk;
-    for (int u = v + 1; u < k - 1; ++u) a.B *= pl->N[u];
+    for (int u = v + 1; u < k - 1; ++u) a.B *= pl->M[u];
     a.Lin = pl->d[v] + 1;
     a.N = pl->N[v];
     a.logN = pl->logN[v];
-    a.Lout = a.N;
+    a.Lout = pl->M[v];
     a.in = cur_in;
     a.in_item_stride = cur_item;
     a.in_prime_stride = cur_prime;

@@ -6,6 +6,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -140,6 +143,7 @@ static void free_plan(polydet_plan_s *pl) {
   cudaFree(pl->d_mhalf);
   cudaFree(pl->d_mfull);
   cudaFree(pl->d_status);
+  cudaFree(pl->d_vinv);
   delete pl;
 }
 
@@ -165,7 +169,7 @@ static int upload(T **dst, const std::vector<T> &src) {
 extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
                             int nprimes, uint32_t flags) {
   if (!out || n < 1 || n > POLYDET_MAX_N || nvars < 1 || nvars > POLYDET_MAX_VARS ||
-      !entry_deg || flags != 0)
+      !entry_deg || (flags & ~POLYDET_FLAG_FULL_GRID))
     return POLYDET_EINVAL;
   const auto &table = prime_table();
   if (nprimes < 1) return POLYDET_EINVAL;
@@ -197,7 +201,8 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
     while ((1 << lg) < pl->N[v]) ++lg;
     pl->logN[v] = lg;
     pl->E *= (int64_t)(pl->d[v] + 1);
-    pl->G *= pl->N[v];
+    pl->M[v] = (flags & POLYDET_FLAG_FULL_GRID) ? pl->N[v] : pl->D[v] + 1;
+    pl->G *= pl->M[v];
     pl->C *= (int64_t)(pl->D[v] + 1);
     pl->tw_off[v] = off;
     off += (pl->N[v] + 1) / 2;
@@ -276,15 +281,74 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
   // interpolation all passes but the last, ping-ponging between two halves.
   int64_t n2 = (int64_t)n * n;
   uint64_t eval_slot = 0, interp_slot = 0;
-  for (int v = 1; v < nvars; v += 2) {  // eval pass v output: prod_{u<v} L_u * prod_{u>=v} N_u
+  for (int v = 1; v < nvars; v += 2) {  // eval pass v output: prod_{u<v} L_u * prod_{u>=v} M_u
     uint64_t s = 1;
-    for (int u = 0; u < nvars; ++u) s *= (u < v) ? (uint64_t)(pl->d[u] + 1) : (uint64_t)pl->N[u];
+    for (int u = 0; u < nvars; ++u) s *= (u < v) ? (uint64_t)(pl->d[u] + 1) : (uint64_t)pl->M[u];
     if (s > eval_slot) eval_slot = s;
   }
-  for (int v = 1; v < nvars; ++v) {  // interp pass v output: prod_{u<v} N_u * prod_{u>=v} (D_u+1)
+  for (int v = 1; v < nvars; ++v) {  // interp pass v output: prod_{u<v} M_u * prod_{u>=v} (D_u+1)
     uint64_t s = 1;
-    for (int u = 0; u < nvars; ++u) s *= (u < v) ? (uint64_t)pl->N[u] : (uint64_t)(pl->D[u] + 1);
+    for (int u = 0; u < nvars; ++u) s *= (u < v) ? (uint64_t)pl->M[u] : (uint64_t)(pl->D[u] + 1);
     if (s > interp_slot) interp_slot = s;
+  }
+
+  // Node grid: inverse of the Vandermonde matrix of the nodes x_i = w^i,
+  // i <= D (Sec. 3.3: the interpolating polynomial of degree <= D through
+  // D + 1 distinct nodes is unique).  With m(x) = prod_j (x - x_j) and
+  // q_i(x) = m(x) / (x - x_i) (synthetic division), the Lagrange basis is
+  // q_i / q_i(x_i), so V^-1[e][i] = [x^e] q_i / q_i(x_i).  O(D^2) per table.
+  std::vector<uint32_t> vinv;
+  pl->full = (flags & POLYDET_FLAG_FULL_GRID) ? 1 : 0;
+  if (!pl->full) {
+    int off2 = 0;
+    for (int v = 0; v < nvars; ++v) {
+      pl->vinv_off[v] = off2;
+      off2 += pl->M[v] * pl->M[v];
+    }
+    pl->vinv_len = off2;
+    vinv.assign((size_t)nprimes * off2, 0u);
+    for (int q = 0; q < nprimes; ++q) {
+      const uint64_t p = table[q];
+      for (int v = 0; v < nvars; ++v) {
+        const int m = pl->M[v];
+        uint32_t *dst0 = vinv.data() + (size_t)q * off2 + pl->vinv_off[v];
+        // tables depend on (p, w, m) only: compute each once per process
+        static std::mutex vmu;
+        static std::map<std::tuple<uint32_t, uint32_t, int>, std::vector<uint32_t>> vcache;
+        const auto key = std::make_tuple((uint32_t)p, pl->roots[q][v], m);
+        {
+          std::lock_guard<std::mutex> lock(vmu);
+          auto it = vcache.find(key);
+          if (it != vcache.end()) {
+            memcpy(dst0, it->second.data(), (size_t)m * m * sizeof(uint32_t));
+            continue;
+          }
+        }
+        std::vector<uint64_t> x(m), mc(m + 1, 0), qc(m);
+        uint64_t w = 1;
+        for (int i = 0; i < m; ++i) {
+          x[i] = w;
+          w = w * pl->roots[q][v] % p;
+        }
+        mc[0] = 1;  // m(x), built factor by factor; mc[k] = coefficient of x^k
+        for (int j = 0; j < m; ++j) {
+          for (int k = j + 1; k >= 1; --k) mc[k] = (mc[k - 1] + (p - x[j]) * mc[k]) % p;
+          mc[0] = (p - x[j]) * mc[0] % p;
+        }
+        uint32_t *dst = vinv.data() + (size_t)q * off2 + pl->vinv_off[v];
+        for (int i = 0; i < m; ++i) {
+          qc[m - 1] = 1;  // q_i = m / (x - x_i): q_{k-1} = m_k + x_i q_k
+          for (int k = m - 1; k >= 1; --k) qc[k - 1] = (mc[k] + x[i] * qc[k]) % p;
+          uint64_t den = 0;  // q_i(x_i) by Horner
+          for (int k = m - 1; k >= 0; --k) den = (den * x[i] + qc[k]) % p;
+          const uint64_t inv = h_powmod((uint32_t)den, p - 2, (uint32_t)p);
+          for (int e = 0; e < m; ++e)
+            dst[(size_t)e * m + i] = h_mont((uint32_t)(qc[e] * inv % p), (uint32_t)p);
+        }
+        std::lock_guard<std::mutex> lock(vmu);
+        vcache.emplace(key, std::vector<uint32_t>(dst, dst + (size_t)m * m));
+      }
+    }
   }
   pl->eval_ws_words = eval_slot * (uint64_t)n2;
   pl->interp_ws_words = 2 * interp_slot;
@@ -294,7 +358,8 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
       (rc = upload(&pl->d_tw_inv, twi)) || (rc = upload(&pl->d_ninv, ninv)) ||
       (rc = upload(&pl->d_rn, rn)) || (rc = upload(&pl->d_garner, garner)) ||
       (rc = upload(&pl->d_mhalf, H)) || (rc = upload(&pl->d_mfull, M)) ||
-      (rc = upload(&pl->d_status, std::vector<uint32_t>(1, 0u)))) {
+      (rc = upload(&pl->d_status, std::vector<uint32_t>(1, 0u))) ||
+      (!pl->full && (rc = upload(&pl->d_vinv, vinv)))) {
     free_plan(pl);
     return rc;
   }
@@ -322,7 +387,9 @@ extern "C" int polydet_plan_query(polydet_plan_t pl, polydet_plan_info *info) {
     info->d[v] = pl->d[v];
     info->D[v] = pl->D[v];
     info->N[v] = pl->N[v];
+    info->M[v] = pl->M[v];
   }
+  info->flags = pl->full ? POLYDET_FLAG_FULL_GRID : 0u;
   info->eval_ws_words = pl->eval_ws_words;
   info->interp_ws_words = pl->interp_ws_words;
   return POLYDET_OK;

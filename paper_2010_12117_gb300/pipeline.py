@@ -44,7 +44,7 @@ def _chunk(plan: Plan, budget_bytes: int) -> int:
 def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] = None,
                 store: Optional[ResidueStore] = None, budget_bytes: int = 8 << 30,
                 stream: Optional[torch.cuda.Stream] = None,
-                stop_after_chunks: Optional[int] = None) -> DetResult:
+                stop_after_chunks: Optional[int] = None, full_grid: bool = False) -> DetResult:
     """Exact det of the polynomial matrix ``coeffs`` [n][n][E] (lex encoding
     of Sec. 2) with entry degrees ``degs``; returns its coefficients."""
     coeffs = np.asarray(coeffs)
@@ -54,7 +54,7 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
     if np.abs(coeffs).max(initial=0) >= 2 ** 31:
         raise ValueError("coefficients must fit in int32")
     P = nprimes if nprimes is not None else prime_count(coeffs)
-    plan = Plan(n, degs, P)
+    plan = Plan(n, degs, P, full_grid=full_grid)
     dev = torch.device("cuda")
     st = stream if stream is not None else torch.cuda.current_stream()
     with torch.cuda.stream(st):
@@ -63,7 +63,7 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
         todo = list(range(P))
         if store is not None:
             store.open_job({"n": n, "degs": [int(d) for d in degs], "primes": plan.primes,
-                            "input": input_digest(coeffs, degs)})
+                            "full_grid": bool(full_grid), "input": input_digest(coeffs, degs)})
             for q, r in store.done(P, plan.C).items():
                 residues[q * plan.C:(q + 1) * plan.C].copy_(torch.from_numpy(r.view(np.int32)))
                 todo.remove(q)

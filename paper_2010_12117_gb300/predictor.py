@@ -66,7 +66,7 @@ def analytic(s: Shape) -> tuple:
     """(seconds, bytes): roofline time and exact buffer bytes of the batched form."""
     n, k, P = s.n, s.k, s.P
     D = [n * d for d in s.degs]
-    N = [_nextpow2(x + 1) for x in D]
+    N = [x + 1 for x in D]  # evaluation nodes per variable (node grid)
     G = math.prod(N)
     C = math.prod(x + 1 for x in D)
     E = math.prod(d + 1 for d in s.degs)

@@ -50,12 +50,12 @@ def condense_updates(n: int) -> int:
 
 class PlainRunner:
     def __init__(self, mats: Sequence, nprimes: Optional[Sequence[int]] = None,
-                 budget_bytes: int = 6 << 30, device: str = "cuda"):
+                 budget_bytes: int = 6 << 30, device: str = "cuda", full_grid: bool = False):
         self.mats = list(mats)
         self.plans: List[Plan] = []
         for i, pm in enumerate(self.mats):
             P = nprimes[i] if nprimes is not None else prime_count(pm.coeffs)
-            self.plans.append(Plan(pm.n, pm.degs, P))
+            self.plans.append(Plan(pm.n, pm.degs, P, full_grid=full_grid))
         self.dev = torch.device(device)
         co, ro, lo = [0], [0], [0]
         for pm, pl in zip(self.mats, self.plans):
@@ -164,12 +164,13 @@ class BatchedRunner:
     CRT), optionally captured once in a CUDA graph and replayed."""
 
     def __init__(self, mats: Sequence, nprimes: Optional[Sequence[int]] = None,
-                 device: str = "cuda", tune: bool = True, stream: Optional[torch.cuda.Stream] = None):
+                 device: str = "cuda", tune=True, stream: Optional[torch.cuda.Stream] = None,
+                 full_grid: bool = False):
         from .binding import Batch
         self.mats = list(mats)
         Ps = [nprimes[i] if nprimes is not None else prime_count(pm.coeffs)
               for i, pm in enumerate(self.mats)]
-        self.batch = Batch([(pm.n, pm.degs, P) for pm, P in zip(self.mats, Ps)])
+        self.batch = Batch([(pm.n, pm.degs, P) for pm, P in zip(self.mats, Ps)], full_grid=full_grid)
         self.dev = torch.device(device)
         w = self.batch.words
         self.coeffs_dev = torch.empty(max(1, w["coeffs"]), dtype=torch.int32, device=self.dev)

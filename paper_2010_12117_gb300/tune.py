@@ -21,7 +21,7 @@ CACHE = os.path.join(CACHE_DIR, "fused_launch.json")
 
 
 def team(n: int) -> int:
-    return 1 if n <= 12 else (2 if n <= 16 else (4 if n <= 20 else 8))
+    return 1 if n <= 8 else (2 if n <= 11 else (4 if n <= 16 else (8 if n <= 24 else 16)))
 
 
 def candidates(n: int):

@@ -18,10 +18,10 @@ def _lib():
     ensure_lib()
 
 
-def batched_results(mats, tune=False, graph=False, replays=1):
+def batched_results(mats, tune=False, graph=False, replays=1, full_grid=False):
     from paper_2010_12117_gb300.runner import BatchedRunner
     st = torch.cuda.Stream()
-    r = BatchedRunner(mats, tune=tune, stream=st)
+    r = BatchedRunner(mats, tune=tune, stream=st, full_grid=full_grid)
     r.upload(st)
     if graph:
         r.capture(st)
@@ -61,6 +61,11 @@ def test_mixed_orders_match_plain_and_oracle():
         cost = pm.n ** 3 * np.prod([pm.n * d + 1 for d in pm.degs])
         if cost < 2e6:
             assert g == bareiss.det_packed(pm.coeffs.tolist(), pm.degs), (pm.n, pm.degs)
+
+
+def test_full_grid_batch_equals_node_grid_batch():
+    mats = _mixed()[:16]
+    assert batched_results(mats, full_grid=True) == batched_results(mats)
 
 
 def test_graph_replay_and_tuning_do_not_change_results():

@@ -80,6 +80,18 @@ def test_sparse_12x12_xyz_full_size(nprimes):
         assert got.P == 20
 
 
+@pytest.mark.parametrize("maker", [lambda: synth.dense_4x4(3), lambda: synth.sylvester_16(4),
+                                   lambda: synth.random_matrix(np.random.default_rng(2), 5, (2, 1, 2),
+                                                               0.5, -99, 100)])
+def test_full_grid_and_node_grid_agree_with_the_oracle(maker):
+    """The paper's full power-of-two grid with inverse NTT and the node grid
+    with inverse Vandermonde give the oracle's determinant."""
+    pm = maker()
+    want = bareiss.det_packed(pm.coeffs.tolist(), pm.degs)
+    assert det(pm, full_grid=True).coeffs == want
+    assert det(pm, full_grid=False).coeffs == want
+
+
 def test_extra_primes_and_larger_degree_box_do_not_change_the_result():
     rng = np.random.default_rng(77)
     pm = synth.random_matrix(rng, 5, (2, 1), 0.6, -1000, 1000)

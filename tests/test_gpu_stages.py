@@ -20,9 +20,9 @@ def _lib():
     ensure_lib()
 
 
-def Plan(n, degs, P):
+def Plan(n, degs, P, full_grid=False):
     from paper_2010_12117_gb300.binding import Plan as _P
-    return _P(n, degs, P)
+    return _P(n, degs, P, full_grid=full_grid)
 
 
 def u32(t):
@@ -33,27 +33,33 @@ def u32(t):
 def test_plan_constants_match_oracle():
     pl = Plan(12, (3, 3, 3), 5)
     assert pl.primes == modular.ntt_primes()[:5]
-    assert pl.D == (36, 36, 36) and pl.N == (64, 64, 64)
-    assert pl.G == 64 ** 3 and pl.C == 37 ** 3 and pl.E == 64
+    assert pl.D == (36, 36, 36) and pl.N == (64, 64, 64) and pl.M == (37, 37, 37)
+    assert pl.G == 37 ** 3 and pl.C == 37 ** 3 and pl.E == 64
+    full = Plan(12, (3, 3, 3), 5, full_grid=True)
+    assert full.M == (64, 64, 64) and full.G == 64 ** 3 and full.full_grid
     for q, p in enumerate(pl.primes):
         for v, N in enumerate(pl.N):
             assert pl.roots[q][v] == modular.root_of_unity(p, N)
     assert pl.W == oplan.output_words(pl.primes)
 
 
-@pytest.mark.parametrize("n,degs,P,sample", [
-    (4, (2, 2), 2, None),          # dense 4x4 workload, every node
-    (3, (2, 0, 1), 2, None),       # a variable of degree 0 (N_v = 1)
-    (16, (6,), 3, None),           # Sylvester-sized univariate
-    (5, (3, 1, 2), 2, 300),        # trivariate, sampled nodes
-    (12, (3, 3, 3), 1, 40),        # 12x12 trivariate grid (64^3), sampled
+@pytest.mark.parametrize("n,degs,P,sample,full", [
+    (4, (2, 2), 2, None, False),          # dense 4x4 workload, every node
+    (4, (2, 2), 2, None, True),           # ... on the full power-of-two grid
+    (3, (2, 0, 1), 2, None, False),       # a variable of degree 0 (one node)
+    (3, (2, 0, 1), 2, None, True),
+    (16, (6,), 3, None, False),           # Sylvester-sized univariate
+    (2, (7, 5), 2, None, False),          # 8 coefficients: the LP = 8 coset kernel
+    (5, (3, 1, 2), 2, 300, True),         # trivariate, sampled nodes
+    (12, (3, 3, 3), 1, 40, False),        # 12x12 trivariate grid, sampled
+    (12, (3, 3, 3), 1, 40, True),
 ])
-def test_eval_matches_direct_evaluation(n, degs, P, sample):
+def test_eval_matches_direct_evaluation(n, degs, P, sample, full):
     rng = np.random.default_rng(n + 7 * P)
     pm = synth.random_matrix(rng, n, degs, 0.7, -(2 ** 31), 2 ** 31)
     pm.coeffs[0, 0, 0] = -(2 ** 31)  # extreme int32 values
     pm.coeffs[0, 0, -1] = 2 ** 31 - 1
-    pl = Plan(n, degs, P)
+    pl = Plan(n, degs, P, full_grid=full)
     coeffs = torch.from_numpy(pm.coeffs.astype(np.int32).reshape(-1)).cuda()
     evals = torch.empty(P * n * n * pl.G, dtype=torch.int32, device="cuda")
     pl.eval(coeffs, 0, P, evals, pl.workspace(P))
@@ -69,7 +75,7 @@ def test_eval_matches_direct_evaluation(n, degs, P, sample):
         for e in entries:
             vec = pm.coeffs.reshape(n * n, -1)[e].tolist()
             for g in nodes:
-                idx = modular.grid_index(g, pl.N)
+                idx = modular.grid_index(g, pl.M)
                 assert int(got[q, e, g]) == modular.eval_point(vec, degs, idx, ws, p), (q, e, g)
 
 
@@ -150,11 +156,14 @@ def test_condense_matches_gaussian_elimination(n):
             assert int(got[q, g]) == want, (n, q, g)
 
 
-def test_interp_round_trip_against_oracle():
+@pytest.mark.parametrize("full,degs", [(False, (2, 2)), (True, (2, 2)), (False, (1, 2, 1)),
+                                        (False, (5,))])
+def test_interp_round_trip_against_oracle(full, degs):
     """Interpolation of the oracle's evaluations of a random polynomial of
-    bounded degree returns its coefficients, with a clean status."""
-    n, degs, P = 4, (2, 2), 2
-    pl = Plan(n, degs, P)
+    bounded degree returns its coefficients, with a clean status - on the node
+    grid (inverse Vandermonde) and on the full grid (inverse NTT)."""
+    n, P = 4, 2
+    pl = Plan(n, degs, P, full_grid=full)
     rng = random.Random(17)
     det_vals = np.empty((P, pl.G), dtype=np.uint64)
     want = []
@@ -162,7 +171,7 @@ def test_interp_round_trip_against_oracle():
         p = pl.primes[q]
         vec = [rng.randrange(p) for _ in range(pl.C)]
         want.append(vec)
-        det_vals[q] = modular.eval_grid(vec, pl.D, pl.N, pl.roots[q], p)
+        det_vals[q] = modular.eval_grid(vec, pl.D, pl.M, pl.roots[q], p)
     dv = torch.from_numpy(det_vals.astype(np.uint32).view(np.int32).reshape(-1)).cuda()
     res = torch.empty(P * pl.C, dtype=torch.int32, device="cuda")
     pl.interp(dv, 0, P, res, pl.workspace(P))
@@ -170,9 +179,12 @@ def test_interp_round_trip_against_oracle():
     got = u32(res).reshape(P, pl.C)
     for q in range(P):
         assert got[q].tolist() == want[q]
-    # and against the oracle's inverse DFT directly
-    box, clean = modular.interp_grid(det_vals[0].tolist(), pl.N, pl.roots[0], pl.primes[0], pl.D)
-    assert clean and box == want[0]
+    # and against the oracle's interpolation of the same values directly
+    if full:
+        box, clean = modular.interp_grid(det_vals[0].tolist(), pl.N, pl.roots[0], pl.primes[0], pl.D)
+        assert clean and box == want[0]
+    else:
+        assert modular.interp_nodes(det_vals[0].tolist(), pl.M, pl.roots[0], pl.primes[0]) == want[0]
 
 
 def test_interp_flags_a_degree_bound_violation():
@@ -180,7 +192,7 @@ def test_interp_flags_a_degree_bound_violation():
     nonzero tail: the status word reports it (no fault, no abort)."""
     from paper_2010_12117_gb300.binding import EBOUND, lib
     n, degs, P = 2, (1, 1), 1  # D = (2, 2) inside the 4 x 4 grid: a 7-value tail
-    pl = Plan(n, degs, P)
+    pl = Plan(n, degs, P, full_grid=True)
     assert pl.C < pl.G
     rng = np.random.default_rng(5)
     vals = rng.integers(0, pl.primes[0], pl.G, dtype=np.uint64).astype(np.uint32)

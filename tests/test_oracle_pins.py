@@ -322,6 +322,24 @@ def test_eval_interp_round_trip_and_zero_tail():
     assert not clean2
 
 
+def test_node_grid_interpolation_round_trip():
+    """Values of a random polynomial at the first D_v + 1 powers of omega_v
+    interpolate back to its coefficients (the node grid of the library)."""
+    rng = random.Random(12)
+    p = PRIMES[3]
+    D = (4, 2, 3)
+    Ms = tuple(d + 1 for d in D)
+    Ns = plan.grid_sizes(D)
+    ws = [modular.root_of_unity(p, N) for N in Ns]
+    vec = [rng.randrange(p) for _ in range(prod(Ms))]
+    vals = modular.eval_grid(vec, D, Ms, ws, p)
+    assert modular.interp_nodes(vals, Ms, ws, p) == vec
+    # a different polynomial gives different values (the map is injective)
+    vec2 = list(vec)
+    vec2[7] = (vec2[7] + 1) % p
+    assert modular.eval_grid(vec2, D, Ms, ws, p) != vals
+
+
 def test_eval_matches_per_variable_horner():
     """Grid evaluation against nested Horner in x_k, ..., x_1 (another route)."""
     p = PRIMES[1]
