@@ -1,8 +1,8 @@
 // Determinant mod p of one n x n matrix per grid node (Sec. 3.2, Algorithm 3).
 //
 // A team of T consecutive lanes owns one matrix: lane t holds the columns
-// j = t, t + T, t + 2T, ... entirely in registers (one lane for n <= 8; 2,
-// 4, 8 or 16 lanes up to n = 32).  Every index into the register array
+// j = t, t + T, t + 2T, ... entirely in registers (one lane for n <= 14; 2,
+// 4 or 8 lanes up to n = 32).  Every index into the register array
 // is a compile-time constant after unrolling (see TeamFor for the lanes per
 // matrix of each order), so nothing spills to local
 // memory, and there are no barriers: the team talks through warp shuffles.
@@ -28,6 +28,27 @@
 
 #define PD_FULL 0xffffffffu
 
+// Whether lane t's m-th column j = t + T m lies strictly between lo and NN.
+// After unrolling m and lo are constants, so every part that does not depend
+// on t folds away: columns wholly inside or outside the range cost nothing,
+// only the one column block that straddles `lo` keeps a run-time test.
+template <int NN, int T>
+PD_D bool col_in(int t, int m, int lo) {
+  const int jmin = T * m, jmax = T * m + T - 1;
+  if (jmin > lo && jmax < NN) return true;
+  if (jmax <= lo || jmin >= NN) return false;
+  const int j = jmin + t;
+  return j > lo && j < NN;
+}
+
+// One lane per determinant: the (numerator, denominator) pair of the
+// elimination gives det(A) = R^n num / den (see ElimStep), finished by one
+// Fermat inversion.
+PD_D uint32_t finish_det(uint32_t Q, uint32_t den, const ModP &md, uint32_t rn) {
+  const uint32_t inv = mpow(den, md.p - 2u, md.r1, md.p, md.pinv);
+  return mmul(mmul(Q, inv, md.p, md.pinv), rn, md.p, md.pinv);
+}
+
 // One elimination step c, with c a template parameter so that every index
 // into the register array is a compile-time constant.
 template <int NN, int T, int c>
@@ -48,8 +69,7 @@ struct ElimStep {
         const bool fix = (piv == 0u) && (r < NN);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          const int j = t + T * m;
-          if (j >= c && j < NN) {
+          if (col_in<NN, T>(t, m, c - 1)) {
             uint32_t add = 0u;
 #pragma unroll
             for (int i = c + 1; i < NN; ++i) add = (i == r) ? a[m][i] : add;
@@ -64,8 +84,7 @@ struct ElimStep {
         f[i] = (T == 1) ? a[mc][i] : __shfl_sync(PD_FULL, a[mc][i], owner, T);
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        const int j = t + T * m;
-        if (j > c && j < NN) {
+        if (col_in<NN, T>(t, m, c)) {
           const uint32_t acj = a[m][c];
 #pragma unroll
           for (int i = c + 1; i < NN; ++i) a[m][i] = mfms(piv, a[m][i], f[i], acj, p, pinv);
@@ -86,6 +105,67 @@ struct ElimStep<NN, T, NN> {
   static PD_D void run(uint32_t (&)[M][NN], int, uint32_t, uint32_t, uint32_t &, uint32_t &) {}
 };
 
+// The same elimination without the pivot search: no warp vote per step, so
+// the steps overlap freely (the vote is a convergence point on every step).
+// A zero pivot is only recorded in `zero`; the caller then redoes the whole
+// matrix with ElimStep.  For matrices with nonzero leading minors - almost
+// every node of a random polynomial matrix mod a 31-bit prime - the result
+// is the one ElimStep computes.
+template <int NN, int T, int c>
+struct FastStep {
+  static constexpr int M = (NN + T - 1) / T;
+  static PD_D void run(uint32_t (&a)[M][NN], int t, uint32_t p, uint32_t pinv, uint32_t &Q,
+                       uint32_t &den, bool &zero) {
+    constexpr int owner = c % T;
+    constexpr int mc = c / T;
+    const uint32_t piv = (T == 1) ? a[mc][c] : __shfl_sync(PD_FULL, a[mc][c], owner, T);
+    zero |= (piv == 0u);
+    if (c < NN - 1) {
+      uint32_t f[NN];
+#pragma unroll
+      for (int i = c + 1; i < NN; ++i)
+        f[i] = (T == 1) ? a[mc][i] : __shfl_sync(PD_FULL, a[mc][i], owner, T);
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        if (col_in<NN, T>(t, m, c)) {
+          const uint32_t acj = a[m][c];
+#pragma unroll
+          for (int i = c + 1; i < NN; ++i) a[m][i] = mfms(piv, a[m][i], f[i], acj, p, pinv);
+        }
+      }
+      Q = mmul(Q, piv, p, pinv);
+      den = mmul(den, Q, p, pinv);
+      FastStep<NN, T, c + 1>::run(a, t, p, pinv, Q, den, zero);
+    } else {
+      Q = mmul(Q, piv, p, pinv);
+    }
+  }
+};
+
+template <int NN, int T>
+struct FastStep<NN, T, NN> {
+  static constexpr int M = (NN + T - 1) / T;
+  static PD_D void run(uint32_t (&)[M][NN], int, uint32_t, uint32_t, uint32_t &, uint32_t &, bool &) {}
+};
+
+// The pivoting elimination of one matrix read again from `base` (entry
+// (i, j) at base[(i NN + j) stride]).  Kept out of line so that the rare
+// redo does not add to the register pressure of the fast pass.
+template <int NN, int T>
+__device__ __noinline__ uint2 elim_search(const uint32_t *base, int64_t stride, int t, ModP md) {
+  constexpr int M = (NN + T - 1) / T;
+  uint32_t a[M][NN];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = t + T * m;
+#pragma unroll
+    for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? base[(int64_t)(i * NN + j) * stride] : 0u;
+  }
+  uint32_t Q = md.r1, den = md.r1;
+  ElimStep<NN, T, 0>::run(a, t, md.p, md.pinv, Q, den);
+  return make_uint2(Q, den);
+}
+
 template <int NN, int T>
 __global__ void __launch_bounds__(128) condense_kernel(const uint32_t *__restrict__ evals,
                                                        uint32_t *__restrict__ detvals, int64_t G,
@@ -97,7 +177,7 @@ __global__ void __launch_bounds__(128) condense_kernel(const uint32_t *__restric
   const int q = prime_lo + qrel;
   const ModP md = mod[q];
   const uint32_t p = md.p, pinv = md.pinv;
-  const int t = (T == 1) ? 0 : (int)(threadIdx.x % T);
+  const int t = (int)(threadIdx.x & (T - 1));
   const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
   const bool active = g < G;
   const int64_t gg = active ? g : (G - 1);
@@ -112,18 +192,37 @@ __global__ void __launch_bounds__(128) condense_kernel(const uint32_t *__restric
   }
 
   uint32_t Q = md.r1, den = md.r1;
-  ElimStep<NN, T, 0>::run(a, t, p, pinv, Q, den);
-  const uint32_t inv = mpow(den, p - 2u, md.r1, p, pinv);
-  uint32_t res = mmul(Q, inv, p, pinv);
-  res = mmul(res, rn[q], p, pinv);
-  if (active && t == 0) detvals[(int64_t)qrel * G + g] = res;
+  bool zero = false;
+  FastStep<NN, T, 0>::run(a, t, p, pinv, Q, den, zero);
+  if (__any_sync(PD_FULL, zero)) {  // some matrix of this warp met a zero pivot
+    const uint2 qd = elim_search<NN, T>(base, G, t, md);
+    Q = qd.x;
+    den = qd.y;
+  }
+  // Every lane of a team holds the same (Q, den): hand them to one lane per
+  // determinant so that the CTA's inversions run once each, in as few warps
+  // as possible, and the results are stored contiguously.
+  __shared__ uint32_t fin_q[128], fin_d[128];
+  const int S = blockDim.x / T;
+  const int team = threadIdx.x / T;
+  if (t == 0) {
+    fin_q[team] = Q;
+    fin_d[team] = den;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < S) {
+    const int64_t gd = (int64_t)blockIdx.x * S + threadIdx.x;
+    if (gd < G) detvals[(int64_t)qrel * G + gd] = finish_det(fin_q[threadIdx.x], fin_d[threadIdx.x], md, rn[q]);
+  }
+  (void)active;
 }
 
 template <int NN>
 struct TeamFor {
-  // lanes per determinant: keeps the register-resident matrix near 64
-  // words per lane so that four CTAs of 128 threads fit on an SM
-  static constexpr int value = NN <= 8 ? 1 : (NN <= 11 ? 2 : (NN <= 16 ? 4 : (NN <= 24 ? 8 : 16)));
+  // lanes per determinant, from measured elimination rates: one lane as long
+  // as the matrix fits in registers (the fewer lanes, the fewer shuffles and
+  // the more independent updates per lane), more only beyond that
+  static constexpr int value = NN <= 14 ? 1 : (NN <= 18 ? 2 : (NN <= 28 ? 4 : 8));
 };
 
 template <int NN, int HI>

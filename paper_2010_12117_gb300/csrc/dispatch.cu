@@ -78,4 +78,4 @@ int pd_fused_occupancy(int n, int threads, size_t qwords, int *bps) {
   return POLYDET_EINVAL;
 }
 
-int pd_fused_team(int n) { return n <= 8 ? 1 : (n <= 11 ? 2 : (n <= 16 ? 4 : (n <= 24 ? 8 : 16))); }
+int pd_fused_team(int n) { return n <= 14 ? 1 : (n <= 18 ? 2 : (n <= 28 ? 4 : 8)); }

@@ -85,12 +85,29 @@ __device__ __forceinline__ void fused_eval_entries(const uint32_t *qrow, int t, 
   }
 }
 
+// The pivoting elimination of the team's slice, for the rare warp in which
+// the fast pass met a zero pivot; out of line so that it costs the fast pass
+// no registers.
+template <int NN, int T>
+__device__ __noinline__ uint2 fused_det_search(const uint32_t *mine, int bd, int t, ModP md) {
+  constexpr int M = (NN + T - 1) / T;
+  uint32_t a[M][NN];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = t + T * m;
+#pragma unroll
+    for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? mine[(m * NN + i) * bd] : 0u;
+  }
+  uint32_t Q = md.r1, den = md.r1;
+  ElimStep<NN, T, 0>::run(a, t, md.p, md.pinv, Q, den);
+  return make_uint2(Q, den);
+}
+
 // Node g's determinant (one team), from the entries in its slice.  Kept out
 // of line so that the register allocation of this straight-line body is not
 // constrained by the persistent loop around it.
 template <int NN, int T>
-__device__ __noinline__ void fused_det(const uint32_t *mine, int bd, int t, ModP md, uint32_t rn,
-                                       bool write, uint32_t *out) {
+__device__ __noinline__ uint2 fused_det(const uint32_t *mine, int bd, int t, ModP md) {
   constexpr int M = (NN + T - 1) / T;
   const uint32_t p = md.p, pinv = md.pinv;
   uint32_t a[M][NN];
@@ -101,11 +118,11 @@ __device__ __noinline__ void fused_det(const uint32_t *mine, int bd, int t, ModP
     for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? mine[(m * NN + i) * bd] : 0u;
   }
   uint32_t Q = md.r1, den = md.r1;
-  ElimStep<NN, T, 0>::run(a, t, p, pinv, Q, den);
-  const uint32_t inv = mpow(den, p - 2u, md.r1, p, pinv);
-  uint32_t res = mmul(Q, inv, p, pinv);
-  res = mmul(res, rn, p, pinv);
-  if (write) *out = res;
+  bool zero = false;
+  FastStep<NN, T, 0>::run(a, t, p, pinv, Q, den, zero);
+  if (__any_sync(PD_FULL, zero))  // a zero pivot in this warp: redo with the search
+    return fused_det_search<NN, T>(mine, bd, t, md);
+  return make_uint2(Q, den);
 }
 
 template <int NN, int T>
@@ -121,8 +138,9 @@ __global__ void __launch_bounds__(128) fused_kernel(const FusedSeg *__restrict__
   const int bd = blockDim.x;
   uint32_t *ent = reinterpret_cast<uint32_t *>(fused_smem_u4);  // [M * NN][bd]
   uint32_t *qsm = ent + fused_slice_words<NN>(bd);              // [rows][NN2][Lp]
-  const int t = (T == 1) ? 0 : (int)(threadIdx.x % T);
+  const int t = (int)(threadIdx.x & (T - 1));
   const int team = threadIdx.x / T;
+  __shared__ uint32_t fin_q[128], fin_d[128];
   const int S = bd / T;
 
   for (;;) {
@@ -190,8 +208,19 @@ __global__ void __launch_bounds__(128) fused_kernel(const FusedSeg *__restrict__
     uint32_t *mine = ent + threadIdx.x;
     fused_eval_entries<NN, T>(qsm + (grow - row0) * NN2 * Lp, t, X, L, Lp, p, pinv, mine,
                               bd);
-    // 2. elimination in registers
-    fused_det<NN, T>(mine, bd, t, sg.md, sg.rn, active && t == 0, detvals + sg.det_off + g);
+    // 2. elimination in registers; 3. one lane per node finishes its
+    // determinant (one inversion each) and the item's results are stored
+    // contiguously
+    const uint2 qd = fused_det<NN, T>(mine, bd, t, sg.md);
+    if (t == 0) {
+      fin_q[team] = qd.x;
+      fin_d[team] = qd.y;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < S && g0 + threadIdx.x < sg.G)
+      detvals[sg.det_off + g0 + threadIdx.x] =
+          finish_det(fin_q[threadIdx.x], fin_d[threadIdx.x], sg.md, sg.rn);
+    (void)active;
   }
 }
 

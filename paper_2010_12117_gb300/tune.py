@@ -21,7 +21,7 @@ CACHE = os.path.join(CACHE_DIR, "fused_launch.json")
 
 
 def team(n: int) -> int:
-    return 1 if n <= 8 else (2 if n <= 11 else (4 if n <= 16 else (8 if n <= 24 else 16)))
+    return 1 if n <= 14 else (2 if n <= 18 else (4 if n <= 28 else 8))
 
 
 def candidates(n: int):
