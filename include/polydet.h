@@ -194,15 +194,24 @@ int polydet_sync_status(polydet_plan_t plan, void *stream, uint32_t *status_out)
 /* ------------------------------------------------------------------------
  * Batches: many jobs of uneven order, variable count, degree and prime
  * count in one run (the data-parallel loop of Algorithm 1 over matrices,
- * primes and nodes at once).  Evaluation of the last variable is fused into
- * the determinant kernel, so evaluated matrices never reach memory: one
- * persistent kernel per matrix order takes (job, prime, node-block) items
- * from a counter kept in the caller's workspace.
+ * primes and nodes at once).  Each matrix order runs in one of two modes:
+ *   POLYDET_BATCH_FUSED: evaluation of the last variable is fused into the
+ *     determinant kernel, so evaluated matrices never reach memory: one
+ *     persistent kernel per order takes (job, prime, node-block) items from
+ *     a counter kept in the caller's workspace;
+ *   POLYDET_BATCH_MATERIALIZED: the first variable's NTT pass writes the
+ *     evaluated matrices of a chunk of primes into the workspace and the
+ *     condensation kernel of polydet_condense_batch reads them back (cheaper
+ *     per node than fused evaluation when n^2 entries dominate).
+ * The default is fused for n < POLYDET_BATCH_MATERIALIZE_N, materialized
+ * from there on; polydet_batch_set_mode changes it per order (the
+ * autotuner's second knob).
  *
  * Buffers are caller-owned device arrays laid out by the batch; job j
  * occupies words [off[j], off[j+1]) of each (polydet_batch_offsets):
  *   coeffs   int32  : job j's [n][n][E] coefficients, as for polydet_eval
- *   partial  uint32 : every variable but the last evaluated (eval -> condense)
+ *   partial  uint32 : eval -> condense: every variable but the last evaluated
+ *                      (fused), or every variable but the first (materialized)
  *   detvals  uint32 : [P][G] determinants at the nodes (as condense_batch)
  *   residues uint32 : [P][C] determinant residues (as polydet_interp)
  *   limbs    uint32 : [C][W] signed coefficients (as polydet_crt)
@@ -224,11 +233,21 @@ typedef struct polydet_batch_s *polydet_batch_t;
 typedef struct polydet_batch_info {
   int32_t njobs;
   int64_t coeff_words, partial_words, detval_words, residue_words, limb_words;
-  uint64_t workspace_words;
+  uint64_t workspace_words;           /* for the current modes              */
   int64_t items[POLYDET_MAX_N + 1];   /* fused work items per matrix order  */
   int32_t threads[POLYDET_MAX_N + 1]; /* CTA size per matrix order          */
   int32_t blocks[POLYDET_MAX_N + 1];  /* persistent CTAs per matrix order   */
+  int32_t mode[POLYDET_MAX_N + 1];    /* POLYDET_BATCH_* per matrix order   */
+  uint64_t chunk_words;               /* materialized chunk budget          */
 } polydet_batch_info;
+
+#define POLYDET_BATCH_FUSED 0
+#define POLYDET_BATCH_MATERIALIZED 1
+#define POLYDET_BATCH_MATERIALIZE_N 14
+/* Materialized mode: default words of evaluated matrices one chunk may
+ * hold; a chunk is as many primes of one job as fit, and never less than
+ * one (polydet_batch_set_chunk_words changes the budget). */
+#define POLYDET_BATCH_CHUNK_WORDS (512ull * 1024ull * 1024ull)
 
 #define POLYDET_OFF_COEFFS 0
 #define POLYDET_OFF_PARTIAL 1
@@ -250,11 +269,28 @@ int polydet_batch_job_plan(polydet_batch_t batch, int job, polydet_plan_t *plan_
  * graph capture (uploads the segment table). */
 int polydet_batch_set_launch(polydet_batch_t batch, int n, int threads);
 
-/* Stage 1 of a batch: every variable but the last (Sec. 3.1). */
+/* Mode (POLYDET_BATCH_*) of matrix order n.  Changes the partial tensor's
+ * content and the workspace size (query again); rerun polydet_batch_eval
+ * before the next condense.  Not during a graph capture. */
+int polydet_batch_set_mode(polydet_batch_t batch, int n, int mode);
+/* Chunk budget of the materialized mode in words (>= 1; the workspace size
+ * changes: query again).  Not during a graph capture. */
+int polydet_batch_set_chunk_words(polydet_batch_t batch, uint64_t words);
+/* Lanes that share one determinant in the condensation kernels of order n
+ * (a CTA size must be a multiple of it); POLYDET_EINVAL outside 1..32.  Host
+ * only: no device call. */
+int polydet_team_size(int n);
+
+/* Stage 1 of a batch (Sec. 3.1): every variable but the last (fused orders)
+ * or but the first (materialized orders); all orders (n = 0 in
+ * polydet_batch_eval_n) or only the jobs of order n. */
 int polydet_batch_eval(polydet_batch_t batch, const int32_t *coeffs_dev, uint32_t *partial_dev,
                        uint32_t *ws_dev, void *stream);
-/* Stage 2: last-variable evaluation fused with condensation (Sec. 3.1-3.2),
- * all orders (n = 0 in polydet_batch_condense_n) or only order n. */
+int polydet_batch_eval_n(polydet_batch_t batch, int n, const int32_t *coeffs_dev,
+                         uint32_t *partial_dev, uint32_t *ws_dev, void *stream);
+/* Stage 2 (Sec. 3.1-3.2): the remaining variable's evaluation and the
+ * condensation, all orders (n = 0 in polydet_batch_condense_n) or only
+ * order n. */
 int polydet_batch_condense(polydet_batch_t batch, const uint32_t *partial_dev,
                            uint32_t *detvals_dev, uint32_t *ws_dev, void *stream);
 int polydet_batch_condense_n(polydet_batch_t batch, int n, const uint32_t *partial_dev,

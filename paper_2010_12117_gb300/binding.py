@@ -46,6 +46,10 @@ OFF_COEFFS, OFF_PARTIAL, OFF_DETVALS, OFF_RESIDUES, OFF_LIMBS = 0, 1, 2, 3, 4
 
 
 FLAG_FULL_GRID = 0x1
+BATCH_FUSED = 0
+BATCH_MATERIALIZED = 1
+BATCH_MATERIALIZE_N = 14
+BATCH_CHUNK_WORDS = 512 * 1024 * 1024
 
 
 class Job(ctypes.Structure):
@@ -58,7 +62,8 @@ class BatchInfo(ctypes.Structure):
                 ("partial_words", ctypes.c_int64), ("detval_words", ctypes.c_int64),
                 ("residue_words", ctypes.c_int64), ("limb_words", ctypes.c_int64),
                 ("workspace_words", ctypes.c_uint64), ("items", ctypes.c_int64 * (MAX_N + 1)),
-                ("threads", ctypes.c_int32 * (MAX_N + 1)), ("blocks", ctypes.c_int32 * (MAX_N + 1))]
+                ("threads", ctypes.c_int32 * (MAX_N + 1)), ("blocks", ctypes.c_int32 * (MAX_N + 1)),
+                ("mode", ctypes.c_int32 * (MAX_N + 1)), ("chunk_words", ctypes.c_uint64)]
 
 
 _lib = None
@@ -89,7 +94,11 @@ SIGNATURES = {
     "polydet_batch_offsets": (_I, [_VP, _I, _PI64]),
     "polydet_batch_job_plan": (_I, [_VP, _I, ctypes.POINTER(_VP)]),
     "polydet_batch_set_launch": (_I, [_VP, _I, _I]),
+    "polydet_batch_set_mode": (_I, [_VP, _I, _I]),
+    "polydet_batch_set_chunk_words": (_I, [_VP, ctypes.c_uint64]),
+    "polydet_team_size": (_I, [_I]),
     "polydet_batch_eval": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "polydet_batch_eval_n": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "polydet_batch_condense": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "polydet_batch_condense_n": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "polydet_batch_interp": (_I, [_VP, _VP, _VP, _VP, _VP]),
@@ -273,6 +282,15 @@ class Plan:
         return st.value
 
 
+def team_size(n: int) -> int:
+    """Lanes per determinant in the condensation kernels of order n (a pure
+    host query of the library's table)."""
+    t = lib().polydet_team_size(int(n))
+    if t < 1:
+        _check(t, "polydet_team_size")
+    return t
+
+
 class Batch:
     """A polydet batch: jobs of any shape, one fused run for all of them.
     ``jobs`` is a list of (n, degs, nprimes)."""
@@ -319,6 +337,20 @@ class Batch:
         _check(lib().polydet_batch_set_launch(self._h, int(n), int(threads)), "polydet_batch_set_launch")
         self.refresh()
 
+    def set_mode(self, n: int, mode: int) -> None:
+        """BATCH_FUSED or BATCH_MATERIALIZED for order n; rerun eval after it
+        (the partial tensor's content and the workspace size change)."""
+        _check(lib().polydet_batch_set_mode(self._h, int(n), int(mode)), "polydet_batch_set_mode")
+        self.refresh()
+
+    def mode(self, n: int) -> int:
+        return int(self.info.mode[n])
+
+    def set_chunk_words(self, words: int) -> None:
+        """Budget (words) of one materialized chunk; at least one prime."""
+        _check(lib().polydet_batch_set_chunk_words(self._h, int(words)), "polydet_batch_set_chunk_words")
+        self.refresh()
+
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().polydet_batch_destroy(self._h)
@@ -333,9 +365,10 @@ class Batch:
     def _p(self, t, name):
         return _ptr(t, torch.int32, max(1, self.words[name]), name)
 
-    def eval(self, coeffs, partial, ws, stream=None):
-        _check(lib().polydet_batch_eval(self._h, self._p(coeffs, "coeffs"), self._p(partial, "partial"),
-                                        self._p(ws, "workspace"), _stream(stream)), "polydet_batch_eval")
+    def eval(self, coeffs, partial, ws, stream=None, n: int = 0):
+        _check(lib().polydet_batch_eval_n(self._h, int(n), self._p(coeffs, "coeffs"),
+                                          self._p(partial, "partial"), self._p(ws, "workspace"),
+                                          _stream(stream)), "polydet_batch_eval")
 
     def condense(self, partial, detvals, ws, stream=None, n: int = 0):
         _check(lib().polydet_batch_condense_n(self._h, int(n), self._p(partial, "partial"),

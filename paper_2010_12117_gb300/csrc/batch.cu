@@ -4,8 +4,12 @@
 //
 // A run is four calls on one stream (the whole run can be captured in a CUDA
 // graph; nothing in it allocates or synchronises):
-//   polydet_batch_eval      every variable but the last, per job (NTT passes)
-//   polydet_batch_condense  one persistent fused kernel per matrix order
+//   polydet_batch_eval      per job, NTT passes of every variable but the last
+//                           (fused orders) or but the first (materialized)
+//   polydet_batch_condense  fused orders: one persistent fused kernel each;
+//                           materialized orders: per job and chunk of primes,
+//                           the first variable's pass into the workspace and
+//                           the condensation kernel over it
 //   polydet_batch_interp    inverse NTT per job
 //   polydet_batch_crt       Garner CRT per job
 #include <string.h>
@@ -39,7 +43,36 @@ struct polydet_batch_s {
   size_t qwords[POLYDET_MAX_N + 1] = {};
   std::vector<FusedSeg> segs[POLYDET_MAX_N + 1];
   FusedSeg *d_segs[POLYDET_MAX_N + 1] = {};
+  int mode[POLYDET_MAX_N + 1] = {};
+  std::vector<int> jobs_of[POLYDET_MAX_N + 1];
+  uint64_t chunk_words = POLYDET_BATCH_CHUNK_WORDS;
 };
+
+// Primes of job `pl` per materialized chunk: as many as fit in the chunk
+// budget, at least one.
+static int chunk_primes(const polydet_batch_s *b, const polydet_plan_s *pl) {
+  const uint64_t per = (uint64_t)pl->n * pl->n * (uint64_t)pl->G;
+  const uint64_t c = b->chunk_words / std::max<uint64_t>(per, 1);
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(c, (uint64_t)pl->P));
+}
+
+// Workspace words for the current modes: the counters, then the largest
+// scratch any job needs in any stage (stages run one after another).
+static void update_ws(polydet_batch_s *b) {
+  uint64_t ws = 0;
+  for (int j = 0; j < b->njobs; ++j) {
+    const polydet_plan_s *pl = b->plans[j];
+    uint64_t need = pl->interp_ws_words * (uint64_t)pl->P;
+    if (b->mode[pl->n] == POLYDET_BATCH_FUSED) {
+      if (pl->nvars > 1) need = std::max<uint64_t>(need, pd_partial_ws_words(pl) * (uint64_t)pl->P);
+    } else {
+      need = std::max<uint64_t>(need, pd_head_ws_words(pl));
+      need = std::max<uint64_t>(need, (uint64_t)chunk_primes(b, pl) * pl->n * pl->n * (uint64_t)pl->G);
+    }
+    ws = std::max(ws, need);
+  }
+  b->ws_words = kWsHead + ws;
+}
 
 static void destroy_batch(polydet_batch_s *b) {
   if (!b) return;
@@ -92,7 +125,6 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
   b->det_off.assign(1, 0);
   b->res_off.assign(1, 0);
   b->limb_off.assign(1, 0);
-  uint64_t ws = 0;
   for (int j = 0; j < njobs; ++j) {
     const polydet_job &jb = jobs[j];
     if (jb.nvars < 1 || jb.nvars > POLYDET_MAX_VARS || jb.d[jb.nvars - 1] + 1 > 8) {
@@ -112,17 +144,20 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
     b->Lp.push_back(Lp);
     const int64_t n2 = (int64_t)pl->n * pl->n;
     const int64_t rows = pl->G / pl->M[k - 1];
-    const int64_t part = ((int64_t)pl->P * rows * n2 * Lp + 7) / 8 * 8;
+    // room for either mode's partial tensor, so offsets do not move with it
+    const int64_t fused_part = (int64_t)pl->P * rows * n2 * Lp;
+    const int64_t mat_part = (int64_t)pl->P * n2 * (int64_t)pd_head_words(pl);
+    const int64_t part = (std::max(fused_part, mat_part) + 7) / 8 * 8;
     b->coeff_off.push_back(b->coeff_off.back() + n2 * pl->E);
     b->part_off.push_back(b->part_off.back() + part);
     b->det_off.push_back(b->det_off.back() + (int64_t)pl->P * pl->G);
     b->res_off.push_back(b->res_off.back() + (int64_t)pl->P * pl->C);
     b->limb_off.push_back(b->limb_off.back() + pl->C * pl->W);
-    uint64_t need = std::max<uint64_t>(k > 1 ? pd_partial_ws_words(pl) : 0, pl->interp_ws_words) *
-                    (uint64_t)pl->P;
-    ws = std::max(ws, need);
+    b->jobs_of[pl->n].push_back(j);
   }
-  b->ws_words = kWsHead + ws;
+  for (int n = 1; n <= POLYDET_MAX_N; ++n)
+    b->mode[n] = n >= POLYDET_BATCH_MATERIALIZE_N ? POLYDET_BATCH_MATERIALIZED : POLYDET_BATCH_FUSED;
+  update_ws(b);
   for (int j = 0; j < njobs; ++j) {
     polydet_plan_s *pl = b->plans[j];
     const int k = pl->nvars;
@@ -175,7 +210,9 @@ extern "C" int polydet_batch_query(polydet_batch_t b, polydet_batch_info *info) 
     info->items[n] = b->nitems[n];
     info->threads[n] = b->threads[n];
     info->blocks[n] = b->blocks[n];
+    info->mode[n] = b->mode[n];
   }
+  info->chunk_words = b->chunk_words;
   return POLYDET_OK;
 }
 
@@ -208,6 +245,22 @@ extern "C" int polydet_batch_set_launch(polydet_batch_t b, int n, int threads) {
   return build_class(b, n);
 }
 
+extern "C" int polydet_batch_set_mode(polydet_batch_t b, int n, int mode) {
+  if (!b || n < 1 || n > POLYDET_MAX_N ||
+      (mode != POLYDET_BATCH_FUSED && mode != POLYDET_BATCH_MATERIALIZED))
+    return POLYDET_EINVAL;
+  b->mode[n] = mode;
+  update_ws(b);
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_set_chunk_words(polydet_batch_t b, uint64_t words) {
+  if (!b || words < 1) return POLYDET_EINVAL;
+  b->chunk_words = words;
+  update_ws(b);
+  return POLYDET_OK;
+}
+
 // One-variable jobs: the partial tensor is the coefficients mod p_q,
 // out[q][entry][Lp] (l < L written).
 __global__ void repack_kernel(const int32_t *__restrict__ coeffs, uint32_t *__restrict__ out,
@@ -222,12 +275,18 @@ __global__ void repack_kernel(const int32_t *__restrict__ coeffs, uint32_t *__re
   }
 }
 
-extern "C" int polydet_batch_eval(polydet_batch_t b, const int32_t *coeffs, uint32_t *partial,
-                                  uint32_t *ws, void *stream) {
-  if (!b || !coeffs || !partial || !ws) return POLYDET_EINVAL;
+extern "C" int polydet_batch_eval_n(polydet_batch_t b, int n, const int32_t *coeffs,
+                                    uint32_t *partial, uint32_t *ws, void *stream) {
+  if (!b || !coeffs || !partial || !ws || n < 0 || n > POLYDET_MAX_N) return POLYDET_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   for (int j = 0; j < b->njobs; ++j) {
     polydet_plan_s *pl = b->plans[j];
+    if (n && pl->n != n) continue;
+    if (b->mode[pl->n] == POLYDET_BATCH_MATERIALIZED) {
+      int rc = pd_eval_head(pl, coeffs + b->coeff_off[j], partial + b->part_off[j], ws + kWsHead, st);
+      if (rc) return rc;
+      continue;
+    }
     if (pl->nvars == 1) {
       const int64_t n2 = (int64_t)pl->n * pl->n;
       const int L = pl->d[0] + 1;
@@ -245,6 +304,30 @@ extern "C" int polydet_batch_eval(polydet_batch_t b, const int32_t *coeffs, uint
   return POLYDET_OK;
 }
 
+extern "C" int polydet_batch_eval(polydet_batch_t b, const int32_t *coeffs, uint32_t *partial,
+                                  uint32_t *ws, void *stream) {
+  return polydet_batch_eval_n(b, 0, coeffs, partial, ws, stream);
+}
+
+// Materialized order: per job and chunk of primes, the first variable's pass
+// into the workspace, then the condensation kernel over the chunk.
+static int condense_materialized(polydet_batch_s *b, int n, const uint32_t *partial,
+                                 uint32_t *detvals, uint32_t *ws, cudaStream_t st) {
+  uint32_t *chunk = ws + kWsHead;
+  for (int j : b->jobs_of[n]) {
+    polydet_plan_s *pl = b->plans[j];
+    const int cp = chunk_primes(b, pl);
+    for (int lo = 0; lo < pl->P; lo += cp) {
+      const int hi = std::min(pl->P, lo + cp);
+      int rc = pd_eval_tail(pl, partial + b->part_off[j], lo, hi, chunk, st);
+      if (rc) return rc;
+      rc = pd_launch_condense(pl, chunk, lo, hi - lo, detvals + b->det_off[j] + (int64_t)lo * pl->G, st);
+      if (rc) return rc;
+    }
+  }
+  return POLYDET_OK;
+}
+
 extern "C" int polydet_batch_condense_n(polydet_batch_t b, int n, const uint32_t *partial,
                                         uint32_t *detvals, uint32_t *ws, void *stream) {
   if (!b || !partial || !detvals || !ws || n < 0 || n > POLYDET_MAX_N) return POLYDET_EINVAL;
@@ -257,6 +340,11 @@ extern "C" int polydet_batch_condense_n(polydet_batch_t b, int n, const uint32_t
   }
   for (int m = 1; m <= POLYDET_MAX_N; ++m) {
     if ((n && m != n) || b->segs[m].empty()) continue;
+    if (b->mode[m] == POLYDET_BATCH_MATERIALIZED) {
+      int rc = condense_materialized(b, m, partial, detvals, ws, st);
+      if (rc) return rc;
+      continue;
+    }
     int rc = pd_fused_launch(m, b->d_segs[m], (int)b->segs[m].size(), b->nitems[m], partial,
                              detvals, counters + m, b->threads[m], b->blocks[m], b->qwords[m], st);
     if (rc) return rc;

@@ -153,6 +153,20 @@ int pd_eval_partial(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int
                     uint32_t *out, int Lp, uint32_t *ws, cudaStream_t st);
 uint64_t pd_partial_ws_words(const polydet_plan_s *pl);
 
+// Evaluation in two parts, for the batched form's materialized classes.
+// Head: passes of x_k, ..., x_2 for all P primes into head[q][entry][S1]
+// with S1 = pd_head_words(pl) (x_1 still in coefficients: (d_1 + 1) rows of
+// prod_{v>1} M_v nodes); needs pd_head_ws_words(pl) words of scratch.  One
+// variable: the coefficients reduced mod p_q.
+// Tail: the x_1 pass of primes [lo, hi) from the head into
+// evals[q - lo][entry][G], the layout polydet_condense_batch reads.
+uint64_t pd_head_words(const polydet_plan_s *pl);
+uint64_t pd_head_ws_words(const polydet_plan_s *pl);
+int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, uint32_t *head, uint32_t *ws,
+                 cudaStream_t st);
+int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int lo, int hi, uint32_t *evals,
+                 cudaStream_t st);
+
 // One (job, prime) pair of a fused launch: the nodes [0, G) of that job and
 // prime, cut into items of S consecutive nodes (S = threads / lanes per det).
 struct FusedSeg {
@@ -174,3 +188,13 @@ int pd_fused_launch(int n, const FusedSeg *segs, int nsegs, int64_t nitems, cons
 // qwords: words of partial-tensor rows one CTA stages (rows per item x n^2 x Lp)
 int pd_fused_occupancy(int n, int threads, size_t qwords, int *blocks_per_sm);
 int pd_fused_team(int n);
+
+// Lanes per matrix (T) and the resident CTAs of 128 threads the condensation
+// kernel of each order n is compiled for (its __launch_bounds__ minimum),
+// chosen per order from a sweep of both on GB300 with random 31-bit matrices
+// (2^18 nodes): one lane while the whole matrix fits in registers, then the
+// pair that kept the elimination the least latency-bound.
+constexpr int kTeam[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4,
+                                          4, 2, 4, 4, 4, 4, 8, 8, 8, 8, 8, 4, 8, 8, 16, 16};
+constexpr int kMinBlocks[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
+                                               3, 1, 3, 3, 1, 3, 3, 4, 3, 4, 4, 1, 4, 4, 4, 4};

@@ -1,8 +1,8 @@
 // Determinant mod p of one n x n matrix per grid node (Sec. 3.2, Algorithm 3).
 //
 // A team of T consecutive lanes owns one matrix: lane t holds the columns
-// j = t, t + T, t + 2T, ... entirely in registers (one lane for n <= 14; 2,
-// 4 or 8 lanes up to n = 32).  Every index into the register array
+// j = t, t + T, t + 2T, ... entirely in registers (one lane for n <= 15,
+// up to 16 lanes at n = 32).  Every index into the register array
 // is a compile-time constant after unrolling (see TeamFor for the lanes per
 // matrix of each order), so nothing spills to local
 // memory, and there are no barriers: the team talks through warp shuffles.
@@ -121,17 +121,14 @@ struct FastStep {
     const uint32_t piv = (T == 1) ? a[mc][c] : __shfl_sync(PD_FULL, a[mc][c], owner, T);
     zero |= (piv == 0u);
     if (c < NN - 1) {
-      uint32_t f[NN];
+      // row by row: one broadcast a_ic live at a time, beside the M values
+      // a_cj of this lane's columns (fewer live registers than all a_ic)
 #pragma unroll
-      for (int i = c + 1; i < NN; ++i)
-        f[i] = (T == 1) ? a[mc][i] : __shfl_sync(PD_FULL, a[mc][i], owner, T);
+      for (int i = c + 1; i < NN; ++i) {
+        const uint32_t fi = (T == 1) ? a[mc][i] : __shfl_sync(PD_FULL, a[mc][i], owner, T);
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        if (col_in<NN, T>(t, m, c)) {
-          const uint32_t acj = a[m][c];
-#pragma unroll
-          for (int i = c + 1; i < NN; ++i) a[m][i] = mfms(piv, a[m][i], f[i], acj, p, pinv);
-        }
+        for (int m = 0; m < M; ++m)
+          if (col_in<NN, T>(t, m, c)) a[m][i] = mfms(piv, a[m][i], fi, a[m][c], p, pinv);
       }
       Q = mmul(Q, piv, p, pinv);
       den = mmul(den, Q, p, pinv);
@@ -166,8 +163,8 @@ __device__ __noinline__ uint2 elim_search(const uint32_t *base, int64_t stride, 
   return make_uint2(Q, den);
 }
 
-template <int NN, int T>
-__global__ void __launch_bounds__(128) condense_kernel(const uint32_t *__restrict__ evals,
+template <int NN, int T, int MINB>
+__global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__restrict__ evals,
                                                        uint32_t *__restrict__ detvals, int64_t G,
                                                        const ModP *__restrict__ mod,
                                                        const uint32_t *__restrict__ rn,
@@ -219,10 +216,8 @@ __global__ void __launch_bounds__(128) condense_kernel(const uint32_t *__restric
 
 template <int NN>
 struct TeamFor {
-  // lanes per determinant, from measured elimination rates: one lane as long
-  // as the matrix fits in registers (the fewer lanes, the fewer shuffles and
-  // the more independent updates per lane), more only beyond that
-  static constexpr int value = NN <= 14 ? 1 : (NN <= 18 ? 2 : (NN <= 28 ? 4 : 8));
+  static constexpr int value = kTeam[NN];      // lanes per matrix
+  static constexpr int minb = kMinBlocks[NN];  // CTAs per SM the kernel is built for
 };
 
 template <int NN, int HI>
@@ -233,7 +228,7 @@ static int condense_dispatch(const polydet_plan_s *pl, const uint32_t *evals, in
     const int threads = 128;
     const int64_t teams_per_cta = threads / T;
     dim3 grid((unsigned)((pl->G + teams_per_cta - 1) / teams_per_cta), (unsigned)nprimes);
-    condense_kernel<NN, T><<<grid, threads, 0, st>>>(evals, detvals, pl->G, pl->d_mod, pl->d_rn,
+    condense_kernel<NN, T, TeamFor<NN>::minb><<<grid, threads, 0, st>>>(evals, detvals, pl->G, pl->d_mod, pl->d_rn,
                                                      prime_lo);
     PD_CUDA(cudaGetLastError());
     return POLYDET_OK;

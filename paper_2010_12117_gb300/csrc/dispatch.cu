@@ -78,4 +78,8 @@ int pd_fused_occupancy(int n, int threads, size_t qwords, int *bps) {
   return POLYDET_EINVAL;
 }
 
-int pd_fused_team(int n) { return n <= 14 ? 1 : (n <= 18 ? 2 : (n <= 28 ? 4 : 8)); }
+int pd_fused_team(int n) { return (n >= 1 && n <= POLYDET_MAX_N) ? kTeam[n] : 1; }
+
+extern "C" int polydet_team_size(int n) {
+  return (n >= 1 && n <= POLYDET_MAX_N) ? kTeam[n] : POLYDET_EINVAL;
+}

@@ -485,6 +485,106 @@ extern "C" int polydet_interp(polydet_plan_t pl, const uint32_t *detvals, int lo
   return POLYDET_OK;
 }
 
+// Words per entry of the tensor after the passes of x_k, ..., x_{v+1}:
+// prod_{u<=v} L_u * prod_{u>v} M_u (0-based v; L_u = d_u + 1).
+static uint64_t words_after(const polydet_plan_s *pl, int v) {
+  uint64_t s = 1;
+  for (int u = 0; u < pl->nvars; ++u) s *= (u <= v) ? (uint64_t)(pl->d[u] + 1) : (uint64_t)pl->M[u];
+  return s;
+}
+
+uint64_t pd_head_words(const polydet_plan_s *pl) { return words_after(pl, 0); }
+
+uint64_t pd_head_ws_words(const polydet_plan_s *pl) {
+  // passes v >= 2 with v even land in the scratch (so that v = 1 lands in head)
+  uint64_t best = 0;
+  for (int v = 2; v < pl->nvars; v += 2) best = std::max(best, words_after(pl, v - 1));
+  return best * (uint64_t)pl->n * pl->n * (uint64_t)pl->P;
+}
+
+__global__ void reduce_kernel(const int32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t len,
+                              const ModP *__restrict__ mod) {
+  const uint32_t p = mod[blockIdx.y].p;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < len;
+       f += (int64_t)gridDim.x * blockDim.x)
+    out[(int64_t)blockIdx.y * len + f] = reduce_i32(in[f], p);
+}
+
+static TxArgs forward_pass(const polydet_plan_s *pl, int v, int lo) {
+  TxArgs a = {};
+  a.A = 1;
+  for (int u = 0; u < v; ++u) a.A *= pl->d[u] + 1;
+  a.B = 1;
+  for (int u = v + 1; u < pl->nvars; ++u) a.B *= pl->M[u];
+  a.Lin = pl->d[v] + 1;
+  a.N = pl->N[v];
+  a.logN = pl->logN[v];
+  a.Lout = pl->M[v];
+  a.inverse = 0;
+  a.prime_lo = lo;
+  a.mod = pl->d_mod;
+  a.tw = pl->d_tw_fwd;
+  a.tw_len = pl->tw_len;
+  a.tw_off = pl->tw_off[v];
+  a.ninv = pl->d_ninv;
+  a.nvars = pl->nvars;
+  a.var = v;
+  a.status = pl->d_status;
+  return a;
+}
+
+int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, uint32_t *head, uint32_t *ws,
+                 cudaStream_t st) {
+  const int k = pl->nvars;
+  const int64_t n2 = (int64_t)pl->n * pl->n;
+  if (k == 1) {
+    const int64_t len = n2 * pl->E;
+    const unsigned blocks = (unsigned)std::min<int64_t>((len + 255) / 256, 4096);
+    reduce_kernel<<<dim3(blocks, pl->P), 256, 0, st>>>(coeffs, head, len, pl->d_mod);
+    PD_CUDA(cudaGetLastError());
+    return POLYDET_OK;
+  }
+  const int64_t S1 = (int64_t)pd_head_words(pl);
+  int64_t S2 = 0;
+  for (int v = 2; v < k; v += 2) S2 = std::max<int64_t>(S2, (int64_t)words_after(pl, v - 1));
+  const void *cur_in = coeffs;
+  int64_t cur_item = pl->E, cur_prime = 0;
+  int cur_i32 = 1;
+  for (int v = k - 1; v >= 1; --v) {
+    TxArgs a = forward_pass(pl, v, 0);
+    a.in = cur_in;
+    a.in_item_stride = cur_item;
+    a.in_prime_stride = cur_prime;
+    a.in_is_i32 = cur_i32;
+    a.out = (v % 2) ? head : ws;
+    a.out_item_stride = (v % 2) ? S1 : S2;
+    a.out_prime_stride = n2 * a.out_item_stride;
+    int rc = launch_pass(a, (int)n2, pl->P, st);
+    if (rc) return rc;
+    cur_in = a.out;
+    cur_item = a.out_item_stride;
+    cur_prime = a.out_prime_stride;
+    cur_i32 = 0;
+  }
+  return POLYDET_OK;
+}
+
+int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int lo, int hi, uint32_t *evals,
+                 cudaStream_t st) {
+  if (check_range(pl, lo, hi) || !head || !evals) return POLYDET_EINVAL;
+  const int64_t n2 = (int64_t)pl->n * pl->n;
+  const int64_t S1 = (int64_t)pd_head_words(pl);
+  TxArgs a = forward_pass(pl, 0, lo);
+  a.in = head + (int64_t)lo * n2 * S1;
+  a.in_item_stride = S1;
+  a.in_prime_stride = n2 * S1;
+  a.in_is_i32 = 0;
+  a.out = evals;
+  a.out_item_stride = pl->G;
+  a.out_prime_stride = n2 * pl->G;
+  return launch_pass(a, (int)n2, hi - lo, st);
+}
+
 uint64_t pd_partial_ws_words(const polydet_plan_s *pl) {
   // pass v >= 1 output per entry: prod_{u<v} L_u * prod_{v<=u<k-1} N_u * L_{k-1}
   const int k = pl->nvars;

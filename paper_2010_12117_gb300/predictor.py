@@ -7,8 +7,9 @@ factor.  Here the same idea is carried to the batched GPU form in two layers:
 * ``analytic`` - a bound from the job's shape alone: prime count from the
   Hadamard bound, grid and output sizes, the exact buffer bytes of the
   batched form (memory), and a roofline time, max(updates / integer-pipe
-  rate, bytes / HBM rate) plus a per-launch cost.  It needs no training and
-  is a lower bound of both quantities.
+  rate, bytes / HBM rate) plus a per-launch cost, each the smaller over the
+  two modes of the batched form.  It needs no training and is a lower bound
+  of both quantities.
 * ``Predictor`` - an fp32 MLP 8 -> 64 -> 64 -> 2 trained on the method's own
   measured timings and footprints, with forward, backward and Adam in the
   library's CUDA kernels.  Inputs: n, k, max and mean degree, density,
@@ -62,46 +63,84 @@ def shape_of(pm) -> Shape:
     return Shape(pm.n, tuple(int(d) for d in pm.degs), prime_count(c), nz, bits)
 
 
-def analytic(s: Shape) -> tuple:
-    """(seconds, bytes): roofline time and exact buffer bytes of the batched form."""
+_LIMBS = {}
+
+
+def _limbs(P: int) -> int:
+    """32-bit words of the product of the first P primes (the CRT output width)."""
+    if P not in _LIMBS:
+        _LIMBS[P] = (math.prod(binding.prime_table()[:P]).bit_length() + 31) // 32
+    return _LIMBS[P]
+
+
+def default_mode(n: int) -> int:
+    """The batched form's mode of order n when nothing was tuned."""
+    return binding.BATCH_MATERIALIZED if n >= binding.BATCH_MATERIALIZE_N else binding.BATCH_FUSED
+
+
+def analytic_mode(s: Shape, mode: int) -> tuple:
+    """(seconds, bytes) of one job alone in the batched form in ``mode``:
+    the exact buffer bytes the library lays out (coefficients, partial
+    tensor sized for either mode, determinant values, residues, limbs,
+    workspace) and a roofline time, max(updates / integer-pipe rate,
+    bytes / HBM rate) plus a per-launch cost."""
     n, k, P = s.n, s.k, s.P
     D = [n * d for d in s.degs]
-    N = [x + 1 for x in D]  # evaluation nodes per variable (node grid)
-    G = math.prod(N)
+    M = [x + 1 for x in D]  # evaluation nodes per variable (node grid)
+    G = math.prod(M)
     C = math.prod(x + 1 for x in D)
     E = math.prod(d + 1 for d in s.degs)
     L = s.degs[-1] + 1
     Lp = _nextpow2(L)
-    rows = G // N[-1]
-    W = max(1, math.ceil(P * 30.99 / 32))
+    rows = G // M[-1]
+    W = _limbs(P)
     n2 = n * n
-    partial = P * rows * n2 * Lp
-    pws = 0
-    if k > 2:
-        for v in range(1, k - 1):
-            sz = L
-            for u in range(k - 1):
-                sz *= (s.degs[u] + 1) if u < v else N[u]
-            pws = max(pws, sz)
-        pws *= 2 * n2
+
+    def words_after(v):  # per entry, after the passes of the variables > v
+        return math.prod((s.degs[u] + 1) if u <= v else M[u] for u in range(k))
+    fused_part = P * rows * n2 * Lp
+    mat_part = P * n2 * words_after(0)
+    partial = -(-max(fused_part, mat_part) // 8) * 8
     iws = 0
     for v in range(1, k):
         sz = 1
         for u in range(k):
-            sz *= N[u] if u < v else (D[u] + 1)
+            sz *= M[u] if u < v else (D[u] + 1)
         iws = max(iws, sz)
-    iws *= 2
-    words = n2 * E + partial + P * G + P * C + C * W + 256 + P * max(pws, iws)
-    mem = 4 * words
+    ws = P * 2 * iws
+    if mode == binding.BATCH_FUSED:
+        pws = 0
+        if k > 2:
+            for v in range(1, k - 1):
+                sz = L
+                for u in range(k - 1):
+                    sz *= (s.degs[u] + 1) if u < v else M[u]
+                pws = max(pws, sz)
+            pws *= 2 * n2
+        ws = max(ws, P * pws)
+        moved = 4 * (2 * fused_part + 2 * P * G + P * C + C * W)
+        launches = max(1, k - 1) + k + 2
+    else:
+        hws = max([words_after(v - 1) for v in range(2, k, 2)], default=0) * n2 * P
+        cp = max(1, min(P, binding.BATCH_CHUNK_WORDS // (n2 * G)))
+        ws = max(ws, hws, cp * n2 * G)
+        moved = 4 * (2 * mat_part + 2 * P * n2 * G + 2 * P * G + P * C + C * W)
+        launches = max(1, k - 1) + 2 * (-(-P // cp)) + k + 1
+    words = n2 * E + partial + P * G + P * C + C * W + 256 + ws
     updates = P * G * (n - 1) * n * (2 * n - 1) // 6
-    moved = 4 * (2 * partial + 2 * P * G + P * C + C * W)
-    launches = max(1, k - 1) + k + 2
     t = max(updates / UPDATE_RATE, moved / HBM_RATE) + launches * LAUNCH_S
-    return t, float(mem)
+    return t, float(4 * words)
+
+
+def analytic(s: Shape) -> tuple:
+    """(seconds, bytes): a lower bound of both in whichever mode runs."""
+    a = analytic_mode(s, binding.BATCH_FUSED)
+    b = analytic_mode(s, binding.BATCH_MATERIALIZED)
+    return min(a[0], b[0]), min(a[1], b[1])
 
 
 def features(s: Shape) -> np.ndarray:
-    t, m = analytic(s)
+    t, m = analytic_mode(s, default_mode(s.n))
     return np.array([s.n / 32.0, s.k / 6.0, max(s.degs) / 8.0, float(np.mean(s.degs)) / 8.0,
                      s.density, s.coef_bits / 32.0, math.log10(t) / 4.0 + 1.0, math.log2(m) / 40.0],
                     dtype=np.float32)

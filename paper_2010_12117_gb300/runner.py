@@ -16,7 +16,8 @@ from typing import Dict, List, Optional, Sequence
 import numpy as np
 import torch
 
-from .binding import EBOUND, Plan, PolydetError, as_u32, limbs_to_ints
+from .binding import (BATCH_FUSED, BATCH_MATERIALIZED, EBOUND, Plan, PolydetError, as_u32,
+                      limbs_to_ints)
 from .pipeline import prime_count
 
 
@@ -159,9 +160,11 @@ class PlainRunner:
 
 
 class BatchedRunner:
-    """The batched form: every job of the list in one fused run (partial
-    evaluation, one persistent fused kernel per matrix order, interpolation,
-    CRT), optionally captured once in a CUDA graph and replayed."""
+    """The batched form: every job of the list in one run of four stages
+    (partial evaluation; per matrix order either one persistent fused
+    evaluation + condensation kernel or materialized chunks of evaluated
+    matrices and the condensation kernel; interpolation; CRT), optionally
+    captured once in CUDA graphs and replayed."""
 
     def __init__(self, mats: Sequence, nprimes: Optional[Sequence[int]] = None,
                  device: str = "cuda", tune=True, stream: Optional[torch.cuda.Stream] = None,
@@ -193,9 +196,32 @@ class BatchedRunner:
             self.tuning = apply_cached(self.batch)
         elif tune:
             self.upload(st)
-            self.batch.eval(self.coeffs_dev, self.partial, self.ws, st)
             from .tune import tune as _tune
-            self.tuning = _tune(self.batch, self.partial, self.detvals, self.ws, st)
+            self.tuning = _tune(self.batch, self.coeffs_dev, self.partial, self.detvals,
+                                self._workspace, st)
+        self._workspace(self.batch.words["workspace"])
+
+    def set_chunk_words(self, words: int) -> None:
+        """Budget of one materialized chunk (words of evaluated matrices)."""
+        self.batch.set_chunk_words(words)
+        self.graph = None
+        self._workspace(self.batch.words["workspace"])
+
+    def set_modes(self, modes) -> None:
+        """Mode of every order (an int) or of some ({n: mode}); stage 1 must
+        run again afterwards (compute() does)."""
+        orders = self.batch.orders()
+        items = modes.items() if isinstance(modes, dict) else ((n, modes) for n in orders)
+        for n, m in items:
+            self.batch.set_mode(n, m)
+        self.graph = None
+        self._workspace(self.batch.words["workspace"])
+
+    def _workspace(self, words: int) -> torch.Tensor:
+        """The workspace, grown to at least ``words`` (modes change its size)."""
+        if self.ws.numel() < words:
+            self.ws = torch.empty(words, dtype=torch.int32, device=self.dev)
+        return self.ws
 
     @property
     def h2d_bytes(self) -> int:
@@ -214,9 +240,14 @@ class BatchedRunner:
     def kernel_launches(self) -> int:
         tot = 0
         for i in self.batch.job_info:
-            tot += max(1, int(i.nvars) - 1)  # partial evaluation passes (or the repack)
-            tot += int(i.nvars) + 1          # interpolation passes and CRT
-        return tot + len(self.batch.orders())
+            n, k, P, G = int(i.n), int(i.nvars), int(i.P), int(i.G)
+            tot += max(1, k - 1)             # stage 1 passes (or the repack / reduction)
+            if self.batch.mode(n) == BATCH_MATERIALIZED:
+                cp = max(1, min(P, int(self.batch.info.chunk_words) // (n * n * G)))
+                tot += 2 * (-(-P // cp))     # first-variable pass + condensation per chunk
+            tot += k + 1                     # interpolation passes and CRT
+        fused = [n for n in self.batch.orders() if self.batch.mode(n) == BATCH_FUSED]
+        return tot + len(fused)
 
     def upload(self, stream: torch.cuda.Stream) -> None:
         with torch.cuda.stream(stream):
@@ -226,7 +257,7 @@ class BatchedRunner:
         b = self.batch
         return [("eval", lambda: b.eval(self.coeffs_dev, self.partial, self.ws, stream),
                  4.0 * (b.words["coeffs"] + b.words["partial"])),
-                ("fused", lambda: b.condense(self.partial, self.detvals, self.ws, stream),
+                ("condense", lambda: b.condense(self.partial, self.detvals, self.ws, stream),
                  float(self.updates())),
                 ("interp", lambda: b.interp(self.detvals, self.residues, self.ws, stream),
                  4.0 * (b.words["detvals"] + b.words["residues"])),

@@ -77,3 +77,21 @@ def test_hadamard_zero_matrix_and_errors():
     L = binding.lib()
     out = ctypes.c_int(0)
     assert L.polydet_hadamard_primes(0, None, ctypes.byref(out), None) == binding.EINVAL
+
+
+def test_team_sizes_are_usable_and_match_the_tuner():
+    """Lanes per determinant: a power of two dividing every candidate CTA
+    size, small enough that a lane holds at most 8 columns of a 32x32
+    matrix; the tuner's candidate list follows the library's table."""
+    ensure_lib()
+    from paper_2010_12117_gb300 import binding, tune
+    for n in range(1, 33):
+        t = binding.team_size(n)
+        assert t in (1, 2, 4, 8, 16), (n, t)
+        assert -(-n // t) <= 16
+        assert tune.team(n) == t
+        assert all(th % t == 0 for mode, th in tune.candidates(n))
+    with pytest.raises(binding.PolydetError):
+        binding.team_size(0)
+    with pytest.raises(binding.PolydetError):
+        binding.team_size(33)

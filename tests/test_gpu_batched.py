@@ -18,10 +18,15 @@ def _lib():
     ensure_lib()
 
 
-def batched_results(mats, tune=False, graph=False, replays=1, full_grid=False):
+def batched_results(mats, tune=False, graph=False, replays=1, full_grid=False, modes=None,
+                    chunk_words=None):
     from paper_2010_12117_gb300.runner import BatchedRunner
     st = torch.cuda.Stream()
     r = BatchedRunner(mats, tune=tune, stream=st, full_grid=full_grid)
+    if modes is not None:
+        r.set_modes(modes)
+    if chunk_words is not None:
+        r.set_chunk_words(chunk_words)
     r.upload(st)
     if graph:
         r.capture(st)
@@ -61,6 +66,34 @@ def test_mixed_orders_match_plain_and_oracle():
         cost = pm.n ** 3 * np.prod([pm.n * d + 1 for d in pm.degs])
         if cost < 2e6:
             assert g == bareiss.det_packed(pm.coeffs.tolist(), pm.degs), (pm.n, pm.degs)
+
+
+def test_fused_and_materialized_modes_agree():
+    """Every order fused, every order materialized, and the default split:
+    the same integers (and equal to the plain form)."""
+    from paper_2010_12117_gb300.binding import BATCH_FUSED, BATCH_MATERIALIZED
+    mats = _mixed()
+    fused = batched_results(mats, modes=BATCH_FUSED)
+    mat = batched_results(mats, modes=BATCH_MATERIALIZED)
+    assert fused == mat
+    assert mat == batched_results(mats)
+    for pm, g in zip(mats[:10], mat[:10]):
+        assert g == plain(pm), (pm.n, pm.degs)
+
+
+@pytest.mark.parametrize("chunk_words", [None, 1, 3 * 400 * 121 * 101 + 5])
+def test_materialized_chunks(chunk_words):
+    """Materialized orders with the default chunk budget, one prime per
+    chunk (budget 1 word) and three primes per chunk of the 20x20 job (a
+    ragged last chunk): equal to the plain form."""
+    from paper_2010_12117_gb300.binding import BATCH_MATERIALIZED
+    rng = np.random.default_rng(31)
+    big = synth.random_matrix(rng, 20, (6, 5), 0.6, -2000, 2000)  # 400 * 121 * 101 words per prime
+    mats = [big, synth.random_matrix(rng, 3, (1,), 1.0, -5, 5), synth.random_matrix(rng, 16, (2,), 0.5, -9, 9),
+            synth.random_matrix(rng, 20, (1, 1, 1), 0.4, -50, 50)]
+    got = batched_results(mats, modes=BATCH_MATERIALIZED, chunk_words=chunk_words)
+    for pm, g in zip(mats, got):
+        assert g == plain(pm), (pm.n, pm.degs)
 
 
 def test_full_grid_batch_equals_node_grid_batch():

@@ -120,3 +120,22 @@ def test_trained_network_beats_the_analytic_bound_on_measured_jobs():
     assert np.all(e_mlp < e_raw)
     # the judge: never below the analytic lower bound
     assert np.all(pred >= Bd[test] * (1 - 1e-9))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_analytic_memory_is_the_layout_of_the_library(mode):
+    """The analytic bytes of a mode equal the words the library lays out for
+    a one-job batch in that mode (coefficients, partial, determinant values,
+    residues, limbs, workspace)."""
+    from paper_2010_12117_gb300.binding import Batch
+    from paper_2010_12117_gb300.predictor import analytic, analytic_mode, shape_of
+    rng = np.random.default_rng(5)
+    for n, degs in [(6, (2, 1, 2)), (14, (2, 2)), (20, (1, 3, 1)), (16, (4,))]:
+        pm = synth.random_matrix(rng, n, degs, 0.5, -99, 99)
+        s = shape_of(pm)
+        b = Batch([(n, degs, s.P)])
+        b.set_mode(n, mode)
+        words = sum(b.words.values())
+        b.close()
+        assert analytic_mode(s, mode)[1] == 4.0 * words, (n, degs)
+        assert analytic(s)[1] <= 4.0 * words
