@@ -125,53 +125,92 @@ __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
   if (bad) atomicOr(a.status, POLYDET_STATUS_BOUND);
 }
 
-// Forward pass for short inputs (Lin <= LP <= 8): one thread per column,
-// no shared memory.  The N outputs y_i = sum_{e<Lin} c_e w^(i e) are produced
-// coset by coset: for i = j + (N/LP) t, y = DFT_LP(c_e w^(j e))[t] with the
-// LP-th root psi = w^(N/LP), i.e. LP - 1 twiddles and a register DFT of
-// size LP per LP outputs (1 mulmod per output for LP = 4, 1.5 for LP = 8).
-// Consecutive threads hold consecutive columns, so every store of a row is
-// coalesced.
+// Forward pass for short inputs (Lin <= 8): no shared memory.  The N outputs
+// y_i = sum_{e<Lin} c_e w^(i e) are produced coset by coset: for
+// i = j + (N/LP) t (LP = Lin rounded up to a power of two),
+// y = DFT_LP(c_e w^(j e))[t] with the LP-th root psi = w^(N/LP): Lin - 1
+// twiddle products and a register DFT of size LP per LP outputs, in which
+// the LP - Lin inputs that are zero are folded away at compile time.  A
+// thread owns CPT columns (blockDim apart, so every store of a row stays
+// coalesced) and loads each coset's twiddles once for all of them.
 __device__ __forceinline__ uint32_t tw_pow(const uint32_t *tw, int k, int N, uint32_t p) {
   const int h = N >> 1;  // w^(k) for 0 <= k < N from the table of w^j, j < N/2
   return k < h ? __ldg(tw + k) : p - __ldg(tw + (k - h));
 }
 
-template <int LP>
+// x + y and x - y mod p where ZX / ZY say that x / y is known to be zero.
+template <bool ZX, bool ZY>
+PD_D uint32_t add_z(uint32_t x, uint32_t y, uint32_t p) {
+  if (ZY) return x;
+  if (ZX) return y;
+  return addm(x, y, p);
+}
+template <bool ZX, bool ZY>
+PD_D uint32_t sub_z(uint32_t x, uint32_t y, uint32_t p) {
+  if (ZY) return x;
+  if (ZX) return y ? p - y : 0u;
+  return subm(x, y, p);
+}
+
+// DFT_4 of (x0, x1, x2, x3), xe known zero where Ze; r4 = primitive 4th root
+// (Montgomery form).  y_t = sum_e x_e r4^(t e).
+template <bool Z0, bool Z1, bool Z2, bool Z3>
+PD_D void dft4(const uint32_t (&x)[4], uint32_t (&y)[4], uint32_t r4, uint32_t p, uint32_t pinv) {
+  const uint32_t a0 = add_z<Z0, Z2>(x[0], x[2], p), a1 = sub_z<Z0, Z2>(x[0], x[2], p);
+  constexpr bool ZA = Z0 && Z2, ZB = Z1 && Z3;
+  const uint32_t b0 = add_z<Z1, Z3>(x[1], x[3], p);
+  const uint32_t b1 = ZB ? 0u : mmul(r4, sub_z<Z1, Z3>(x[1], x[3], p), p, pinv);
+  y[0] = add_z<ZA, ZB>(a0, b0, p);
+  y[2] = sub_z<ZA, ZB>(a0, b0, p);
+  y[1] = add_z<ZA, ZB>(a1, b1, p);
+  y[3] = sub_z<ZA, ZB>(a1, b1, p);
+}
+
+template <int LIN>
+struct DirectLP {
+  static constexpr int value = LIN <= 1 ? 1 : LIN <= 2 ? 2 : LIN <= 4 ? 4 : 8;
+};
+
+template <int LIN, int CPT>
 __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
+  constexpr int LP = DirectLP<LIN>::value;
   const int q = a.prime_lo + blockIdx.z;
   const ModP md = a.mod[q];
   const uint32_t p = md.p, pinv = md.pinv;
   const int64_t ncols = a.A * a.B;
-  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= ncols) return;
-  const int64_t aa = col / a.B, bb = col - aa * a.B;
+  const int64_t col0 = (int64_t)blockIdx.x * blockDim.x * CPT + threadIdx.x;
+  if (col0 >= ncols) return;
   const int64_t in_base = (int64_t)blockIdx.z * a.in_prime_stride + (int64_t)blockIdx.y * a.in_item_stride;
-  uint32_t c[LP];
-#pragma unroll
-  for (int e = 0; e < LP; ++e) {
-    uint32_t v = 0u;
-    if (e < a.Lin) {
-      const int64_t idx = in_base + (aa * a.Lin + e) * a.B + bb;
-      v = a.in_is_i32 ? reduce_i32(((const int32_t *)a.in)[idx], p) : ((const uint32_t *)a.in)[idx];
-    }
-    c[e] = v;
-  }
   const int N = a.N;
-  const uint32_t *tw = a.tw + (size_t)q * a.tw_len + a.tw_off;
-  // output address of row i of this column
-  int64_t obase, ostride;
-  if (a.il_L) {
-    const int64_t rowrest = bb / a.il_L;
-    obase = (int64_t)blockIdx.z * a.out_prime_stride + (rowrest * a.il_n2 + blockIdx.y) * a.il_Lp + bb % a.il_L;
-    ostride = (a.B / a.il_L) * a.il_n2 * a.il_Lp;  // row r -> row index r * (B / L)
-  } else {
-    obase = (int64_t)blockIdx.z * a.out_prime_stride + (int64_t)blockIdx.y * a.out_item_stride +
-            aa * a.Lout * a.B + bb;
-    ostride = a.B;
-  }
-  uint32_t *out = a.out;
   const int J = N / LP;
+  int64_t ostride;
+  if (a.il_L)
+    ostride = (a.B / a.il_L) * a.il_n2 * a.il_Lp;  // row r -> row index r * (B / L)
+  else
+    ostride = a.B;
+  uint32_t c[CPT][LIN];
+  uint32_t *op[CPT];  // output row 0 of each column (null past the last column)
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int64_t col = col0 + (int64_t)k * blockDim.x;
+    const bool ok = col < ncols;
+    const int64_t cc = ok ? col : col0;
+    const int64_t aa = (a.A == 1) ? 0 : cc / a.B, bb = cc - aa * a.B;
+#pragma unroll
+    for (int e = 0; e < LIN; ++e) {
+      const int64_t idx = in_base + (aa * LIN + e) * a.B + bb;
+      c[k][e] = a.in_is_i32 ? reduce_i32(((const int32_t *)a.in)[idx], p) : ((const uint32_t *)a.in)[idx];
+    }
+    int64_t obase;
+    if (a.il_L)
+      obase = (int64_t)blockIdx.z * a.out_prime_stride + ((bb / a.il_L) * a.il_n2 + blockIdx.y) * a.il_Lp +
+              bb % a.il_L;
+    else
+      obase = (int64_t)blockIdx.z * a.out_prime_stride + (int64_t)blockIdx.y * a.out_item_stride +
+              aa * a.Lout * a.B + bb;
+    op[k] = ok ? a.out + obase : nullptr;
+  }
+  const uint32_t *tw = a.tw + (size_t)q * a.tw_len + a.tw_off;
   uint32_t r4 = 0u, psi1 = 0u, psi2 = 0u, psi3 = 0u;
   if (LP >= 4) r4 = __ldg(tw + (N >> 2));  // w^(N/4), a primitive 4th root
   if (LP == 8) {
@@ -179,42 +218,40 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
     psi2 = r4;
     psi3 = __ldg(tw + 3 * (N >> 3));
   }
+  // rows j + J t < Lout are stored: t < tfull always, t >= tfull while j < lim[t]
+  int lim[LP];
+#pragma unroll
+  for (int t = 0; t < LP; ++t) lim[t] = a.Lout - J * t;
   for (int j = 0; j < J; ++j) {
-    uint32_t z[LP];
-    z[0] = c[0];
+    uint32_t w[LIN];
+    w[0] = md.r1;
 #pragma unroll
-    for (int e = 1; e < LP; ++e) z[e] = (e < a.Lin) ? mmul(tw_pow(tw, j * e, N, p), c[e], p, pinv) : 0u;
-    uint32_t y[LP];
-    if (LP == 1) {
-      y[0] = z[0];
-    } else if (LP == 2) {
-      y[0] = addm(z[0], z[1], p);
-      y[1] = subm(z[0], z[1], p);
-    } else {
-      // DFT_4 of (z0, z2, z4, z6) [LP = 8] or (z0, z1, z2, z3) [LP = 4]
-      const int s = LP / 4;
-      uint32_t E[4];
-      {
-        const uint32_t a0 = addm(z[0], z[2 * s], p), a1 = subm(z[0], z[2 * s], p);
-        const uint32_t b0 = addm(z[s], z[3 * s], p);
-        const uint32_t b1 = mmul(r4, subm(z[s], z[3 * s], p), p, pinv);
-        E[0] = addm(a0, b0, p);
-        E[2] = subm(a0, b0, p);
-        E[1] = addm(a1, b1, p);
-        E[3] = subm(a1, b1, p);
-      }
-      if (LP == 4) {
+    for (int e = 1; e < LIN; ++e) w[e] = tw_pow(tw, j * e, N, p);
+    const int64_t jo = (int64_t)j * ostride;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) y[t] = E[t];
+    for (int k = 0; k < CPT; ++k) {
+      uint32_t z[LP];
+      z[0] = c[k][0];
+#pragma unroll
+      for (int e = 1; e < LP; ++e) z[e] = (e < LIN) ? mmul(w[e], c[k][e], p, pinv) : 0u;
+      uint32_t y[LP];
+      if (LP == 1) {
+        y[0] = z[0];
+      } else if (LP == 2) {
+        y[0] = add_z<false, LIN < 2>(z[0], z[1], p);
+        y[1] = sub_z<false, LIN < 2>(z[0], z[1], p);
+      } else if (LP == 4) {
+        uint32_t x[4] = {z[0], z[1], z[2], z[3 % LP]}, yy[4];
+        dft4<false, false, (LIN <= 2), (LIN <= 3)>(x, yy, r4, p, pinv);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) y[t] = yy[t];
       } else {
-        uint32_t O[4];
-        const uint32_t a0 = addm(z[1], z[5], p), a1 = subm(z[1], z[5], p);
-        const uint32_t b0 = addm(z[3], z[7], p);
-        const uint32_t b1 = mmul(r4, subm(z[3], z[7], p), p, pinv);
-        O[0] = addm(a0, b0, p);
-        O[2] = subm(a0, b0, p);
-        O[1] = addm(a1, b1, p);
-        O[3] = subm(a1, b1, p);
+        // even and odd halves, then y_t = E_t + psi^t O_t, y_{t+4} = E_t - psi^t O_t
+        uint32_t xe[4] = {z[0], z[2 % LP], z[4 % LP], z[6 % LP]};
+        uint32_t xo[4] = {z[1 % LP], z[3 % LP], z[5 % LP], z[7 % LP]};
+        uint32_t E[4], O[4];
+        dft4<false, false, (LIN <= 4), (LIN <= 6)>(xe, E, r4, p, pinv);
+        dft4<false, (LIN <= 3), (LIN <= 5), (LIN <= 7)>(xo, O, r4, p, pinv);
         const uint32_t t1 = mmul(psi1, O[1], p, pinv);
         const uint32_t t2 = mmul(psi2, O[2], p, pinv);
         const uint32_t t3 = mmul(psi3, O[3], p, pinv);
@@ -227,10 +264,13 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
         y[3] = addm(E[3], t3, p);
         y[7] = subm(E[3], t3, p);
       }
-    }
+      if (op[k]) {
+        uint32_t *o = op[k] + jo;
 #pragma unroll
-    for (int t = 0; t < LP; ++t)
-      if (j + J * t < a.Lout) out[obase + (int64_t)(j + J * t) * ostride] = y[t];
+        for (int t = 0; t < LP; ++t)
+          if (j < lim[t]) o[(int64_t)(J * t) * ostride] = y[t];
+      }
+    }
   }
 }
 
@@ -244,13 +284,17 @@ static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
   int64_t ncols = a.A * a.B;
   // short forward transforms over many columns: the register-direct kernel
   if (!a.inverse && a.Lin <= 8 && a.B >= 8) {
-    const int LP = a.Lin <= 1 ? 1 : a.Lin <= 2 ? 2 : a.Lin <= 4 ? 4 : 8;
-    dim3 grid((unsigned)((ncols + 255) / 256), (unsigned)items, (unsigned)nprimes);
-    switch (LP) {
-      case 1: coltx_direct_kernel<1><<<grid, 256, 0, st>>>(a); break;
-      case 2: coltx_direct_kernel<2><<<grid, 256, 0, st>>>(a); break;
-      case 4: coltx_direct_kernel<4><<<grid, 256, 0, st>>>(a); break;
-      default: coltx_direct_kernel<8><<<grid, 256, 0, st>>>(a); break;
+    constexpr int CPT = 4;
+    dim3 grid((unsigned)((ncols + 256 * CPT - 1) / (256 * CPT)), (unsigned)items, (unsigned)nprimes);
+    switch (a.Lin) {
+      case 1: coltx_direct_kernel<1, CPT><<<grid, 256, 0, st>>>(a); break;
+      case 2: coltx_direct_kernel<2, CPT><<<grid, 256, 0, st>>>(a); break;
+      case 3: coltx_direct_kernel<3, CPT><<<grid, 256, 0, st>>>(a); break;
+      case 4: coltx_direct_kernel<4, CPT><<<grid, 256, 0, st>>>(a); break;
+      case 5: coltx_direct_kernel<5, CPT><<<grid, 256, 0, st>>>(a); break;
+      case 6: coltx_direct_kernel<6, CPT><<<grid, 256, 0, st>>>(a); break;
+      case 7: coltx_direct_kernel<7, CPT><<<grid, 256, 0, st>>>(a); break;
+      default: coltx_direct_kernel<8, CPT><<<grid, 256, 0, st>>>(a); break;
     }
     PD_CUDA(cudaGetLastError());
     return POLYDET_OK;

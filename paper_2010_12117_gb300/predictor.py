@@ -16,8 +16,9 @@ factor.  Here the same idea is carried to the batched GPU form in two layers:
   coefficient bits, and the logs of the analytic time and memory; outputs:
   log time and log memory (standardised).  The analytic bound judges it:
   a prediction below the bound is raised to it, one more than ``max_ratio``
-  times the bound falls back to the bound times the calibrated median ratio,
-  and an untrained predictor answers with that calibrated bound.
+  times the larger of the bound and the smallest measured value falls back
+  to the bound times the calibrated median ratio, and an untrained predictor
+  answers with that calibrated bound.
 """
 from __future__ import annotations
 
@@ -158,6 +159,7 @@ class Predictor:
         self.mu = np.zeros(2, dtype=np.float32)
         self.sd = np.ones(2, dtype=np.float32)
         self.ratio = np.ones(2, dtype=np.float64)  # calibrated median actual / bound
+        self.floor = np.zeros(2, dtype=np.float64)  # smallest measured (seconds, bytes)
         self.trained = False
         self.max_ratio = max_ratio
 
@@ -170,6 +172,7 @@ class Predictor:
         self.mu = logy.mean(0).astype(np.float32)
         self.sd = np.maximum(logy.std(0), 1e-3).astype(np.float32)
         self.ratio = np.exp(np.median(logy - np.log(bounds), axis=0))
+        self.floor = np.min(Y, axis=0).astype(np.float64)
         T = ((logy - self.mu) / self.sd).astype(np.float32)
         B = len(X)
         x = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(self.dev)
@@ -208,7 +211,10 @@ class Predictor:
         X = np.stack([features(s) for s in shapes])
         pred = self.raw(X)
         pred = np.maximum(pred, bounds)
-        bad = pred > self.max_ratio * bounds
+        # implausibly large: more than max_ratio times the bound, or than the
+        # smallest footprint / time ever measured when the bound is below it
+        # (allocator granularity and launch latency put a floor under both)
+        bad = pred > self.max_ratio * np.maximum(bounds, self.floor)
         pred[bad] = (bounds * self.ratio)[bad]
         return pred
 
