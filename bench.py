@@ -30,6 +30,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = ("exact poly determinants/sec and mod-p n×n dets/sec; IMAD % and HBM GB/s of peak")
+# DRAM traffic of condense_kernel measured by ncu (read + write over the
+# algorithmic bytes 4 n^2 + 4 per determinant; n = 24 capture, see
+# profiles/condense_kernel_n24_case.md), valid only for the sources it was
+# taken on: the bench reports traffic null once they change.
+CONDENSE_TRAFFIC = {"ratio": 1.016, "sources": {"paper_2010_12117_gb300/csrc/condense.cuh": "df98e5346a17e627",
+                                                "paper_2010_12117_gb300/csrc/common.cuh": "38771a57349238c3"}}
+
+
+def _traffic_ratio():
+    import hashlib
+    for path, h in CONDENSE_TRAFFIC["sources"].items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != h:
+                return None
+    return CONDENSE_TRAFFIC["ratio"]
+
+
 WORKLOAD = ("batched: 256 matrices, n~U[4,24], k~U{1,2,3}, d_v~U[1,4], density~U[0.3,1.0], "
             "int16 coefficients, seeded")
 
@@ -397,6 +414,8 @@ def run_ours(args, world, rank, local):
     plain.compute(st, ptimer)
     torch.cuda.synchronize()
     plain_stage_ms = ptimer.ms()
+    # algorithmic bytes of the condensation launches: 4 n^2 + 4 per determinant
+    cond_bytes = sum(float(pl.P * pl.G) * (4 * pm.n * pm.n + 4) for pm, pl in zip(plain.mats, plain.plans))
     plain.close()
     del plain
 
@@ -431,8 +450,15 @@ def run_ours(args, world, rank, local):
     plain_roofs = roofs_of(plain_stage_ms, dict(ptimer.work))
     # the dominant kernel: the condensation kernel, timed launch by launch
     nl = ptimer.launches["condense"]
+    ratio = _traffic_ratio()
     roof = dict(plain_roofs["condense"], kernel="condense_kernel", launches=nl,
                 avg_launch_ms=plain_stage_ms["condense"] / max(1, nl),
+                traffic=None if ratio is None else ratio * cond_bytes / max(1, nl),
+                traffic_unit="bytes per launch",
+                algorithmic_bytes_per_launch=cond_bytes / max(1, nl),
+                traffic_src=("ncu read + write / algorithmic bytes of the n = 24 capture, scaled to "
+                             "the average launch" if ratio is not None else
+                             "sources changed since the ncu capture"),
                 timed="CUDA events around each of its launches on the launching stream, plain "
                       "pass over the same batch (the batched form's materialized orders run the "
                       "same kernel)")
