@@ -282,6 +282,17 @@ class Plan:
         return st.value
 
 
+def tail_entry_words(M) -> int:
+    """Words per entry of a materialized chunk for node counts M (per
+    variable): rows of the first variable padded to 32 words when they hold
+    at least 64 nodes (the library's layout of the chunk)."""
+    B = 1
+    for m in M[1:]:
+        B *= int(m)
+    Bs = -(-B // 32) * 32 if B >= 64 else B
+    return int(M[0]) * Bs
+
+
 def team_size(n: int) -> int:
     """Lanes per determinant in the condensation kernels of order n (a pure
     host query of the library's table)."""

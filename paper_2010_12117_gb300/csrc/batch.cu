@@ -51,7 +51,7 @@ struct polydet_batch_s {
 // Primes of job `pl` per materialized chunk: as many as fit in the chunk
 // budget, at least one.
 static int chunk_primes(const polydet_batch_s *b, const polydet_plan_s *pl) {
-  const uint64_t per = (uint64_t)pl->n * pl->n * (uint64_t)pl->G;
+  const uint64_t per = (uint64_t)pl->n * pl->n * (uint64_t)pd_tail_layout(pl).entry;
   const uint64_t c = b->chunk_words / std::max<uint64_t>(per, 1);
   return (int)std::max<uint64_t>(1, std::min<uint64_t>(c, (uint64_t)pl->P));
 }
@@ -67,7 +67,8 @@ static void update_ws(polydet_batch_s *b) {
       if (pl->nvars > 1) need = std::max<uint64_t>(need, pd_partial_ws_words(pl) * (uint64_t)pl->P);
     } else {
       need = std::max<uint64_t>(need, pd_head_ws_words(pl));
-      need = std::max<uint64_t>(need, (uint64_t)chunk_primes(b, pl) * pl->n * pl->n * (uint64_t)pl->G);
+      need = std::max<uint64_t>(need, (uint64_t)chunk_primes(b, pl) * pl->n * pl->n *
+                                          (uint64_t)pd_tail_layout(pl).entry);
     }
     ws = std::max(ws, need);
   }
@@ -317,11 +318,13 @@ static int condense_materialized(polydet_batch_s *b, int n, const uint32_t *part
   for (int j : b->jobs_of[n]) {
     polydet_plan_s *pl = b->plans[j];
     const int cp = chunk_primes(b, pl);
+    const EvLayout lay = pd_tail_layout(pl);
     for (int lo = 0; lo < pl->P; lo += cp) {
       const int hi = std::min(pl->P, lo + cp);
-      int rc = pd_eval_tail(pl, partial + b->part_off[j], lo, hi, chunk, st);
+      int rc = pd_eval_tail(pl, partial + b->part_off[j], lo, hi, chunk, lay, st);
       if (rc) return rc;
-      rc = pd_launch_condense(pl, chunk, lo, hi - lo, detvals + b->det_off[j] + (int64_t)lo * pl->G, st);
+      rc = pd_launch_condense(pl, chunk, lay, lo, hi - lo, detvals + b->det_off[j] + (int64_t)lo * pl->G,
+                              st);
       if (rc) return rc;
     }
   }

@@ -142,7 +142,14 @@ void pd_set_error(const char *what, cudaError_t e);
   } while (0)
 
 // Launchers implemented in separate translation units.
-int pd_launch_condense(const polydet_plan_s *pl, const uint32_t *evals, int prime_lo,
+// Where node g's evaluated matrix sits: entry e of node g of prime slot q at
+// q * n^2 * entry + e * entry + (g / rowlen) * rowstride + g % rowlen.  The
+// public layout [P][n^2][G] is {G, G, G}; the batched form's materialized
+// chunks pad each row of the first variable to 128 bytes.
+struct EvLayout {
+  int64_t rowlen, rowstride, entry;
+};
+int pd_launch_condense(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay, int prime_lo,
                        int nprimes, uint32_t *detvals, cudaStream_t st);
 
 // Evaluation of every variable but the last (x_k), for the fused kernels:
@@ -165,7 +172,10 @@ uint64_t pd_head_ws_words(const polydet_plan_s *pl);
 int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, uint32_t *head, uint32_t *ws,
                  cudaStream_t st);
 int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int lo, int hi, uint32_t *evals,
-                 cudaStream_t st);
+                 EvLayout lay, cudaStream_t st);
+// The tail's layout: rows of the first variable padded to 32 words when a
+// row holds at least 64 nodes (aligned rows store at full bandwidth).
+EvLayout pd_tail_layout(const polydet_plan_s *pl);
 
 // One (job, prime) pair of a fused launch: the nodes [0, G) of that job and
 // prime, cut into items of S consecutive nodes (S = threads / lanes per det).
@@ -195,6 +205,6 @@ int pd_fused_team(int n);
 // (2^18 nodes): one lane while the whole matrix fits in registers, then the
 // pair that kept the elimination the least latency-bound.
 constexpr int kTeam[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4,
-                                          4, 2, 4, 4, 4, 4, 8, 8, 8, 8, 8, 4, 8, 8, 16, 16};
+                                          2, 2, 4, 4, 4, 4, 4, 8, 8, 8, 4, 4, 8, 8, 8, 16};
 constexpr int kMinBlocks[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
-                                               3, 1, 3, 3, 1, 3, 3, 4, 3, 4, 4, 1, 4, 4, 4, 4};
+                                               3, 1, 4, 3, 3, 3, 3, 4, 3, 3, 1, 1, 3, 3, 3, 4};

@@ -127,8 +127,18 @@ struct FastStep {
       for (int i = c + 1; i < NN; ++i) {
         const uint32_t fi = (T == 1) ? a[mc][i] : __shfl_sync(PD_FULL, a[mc][i], owner, T);
 #pragma unroll
-        for (int m = 0; m < M; ++m)
-          if (col_in<NN, T>(t, m, c)) a[m][i] = mfms(piv, a[m][i], fi, a[m][c], p, pinv);
+        for (int m = 0; m < M; ++m) {
+          // blocks of columns wholly right of c update unconditionally; the
+          // one block that straddles c keeps its old values by a select, so
+          // the whole elimination stays one branch-free block of code
+          if (T * m > c && T * m + T - 1 < NN) {
+            a[m][i] = mfms(piv, a[m][i], fi, a[m][c], p, pinv);
+          } else if (!(T * m + T - 1 <= c || T * m >= NN)) {
+            const uint32_t v = mfms(piv, a[m][i], fi, a[m][c], p, pinv);
+            const int j = T * m + t;
+            a[m][i] = (j > c && j < NN) ? v : a[m][i];
+          }
+        }
       }
       Q = mmul(Q, piv, p, pinv);
       den = mmul(den, Q, p, pinv);
@@ -166,6 +176,7 @@ __device__ __noinline__ uint2 elim_search(const uint32_t *base, int64_t stride, 
 template <int NN, int T, int MINB>
 __global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__restrict__ evals,
                                                        uint32_t *__restrict__ detvals, int64_t G,
+                                                       EvLayout lay,
                                                        const ModP *__restrict__ mod,
                                                        const uint32_t *__restrict__ rn,
                                                        int prime_lo) {
@@ -178,21 +189,23 @@ __global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__r
   const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
   const bool active = g < G;
   const int64_t gg = active ? g : (G - 1);
-  const uint32_t *base = evals + (int64_t)qrel * NN * NN * G + gg;
+  const int64_t row = gg / lay.rowlen;
+  const int64_t Gs = lay.entry;  // stride between the entries of one node
+  const uint32_t *base = evals + (int64_t)qrel * NN * NN * Gs + row * lay.rowstride + (gg - row * lay.rowlen);
 
   uint32_t a[M][NN];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const int j = t + T * m;
 #pragma unroll
-    for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? __ldg(base + (int64_t)(i * NN + j) * G) : 0u;
+    for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? __ldg(base + (int64_t)(i * NN + j) * Gs) : 0u;
   }
 
   uint32_t Q = md.r1, den = md.r1;
   bool zero = false;
   FastStep<NN, T, 0>::run(a, t, p, pinv, Q, den, zero);
   if (__any_sync(PD_FULL, zero)) {  // some matrix of this warp met a zero pivot
-    const uint2 qd = elim_search<NN, T>(base, G, t, md);
+    const uint2 qd = elim_search<NN, T>(base, Gs, t, md);
     Q = qd.x;
     den = qd.y;
   }
@@ -221,18 +234,18 @@ struct TeamFor {
 };
 
 template <int NN, int HI>
-static int condense_dispatch(const polydet_plan_s *pl, const uint32_t *evals, int prime_lo,
-                             int nprimes, uint32_t *detvals, cudaStream_t st) {
+static int condense_dispatch(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay,
+                             int prime_lo, int nprimes, uint32_t *detvals, cudaStream_t st) {
   if (pl->n == NN) {
     constexpr int T = TeamFor<NN>::value;
     const int threads = 128;
     const int64_t teams_per_cta = threads / T;
     dim3 grid((unsigned)((pl->G + teams_per_cta - 1) / teams_per_cta), (unsigned)nprimes);
-    condense_kernel<NN, T, TeamFor<NN>::minb><<<grid, threads, 0, st>>>(evals, detvals, pl->G, pl->d_mod, pl->d_rn,
-                                                     prime_lo);
+    condense_kernel<NN, T, TeamFor<NN>::minb><<<grid, threads, 0, st>>>(evals, detvals, pl->G, lay,
+                                                                        pl->d_mod, pl->d_rn, prime_lo);
     PD_CUDA(cudaGetLastError());
     return POLYDET_OK;
   }
-  if constexpr (NN < HI) return condense_dispatch<NN + 1, HI>(pl, evals, prime_lo, nprimes, detvals, st);
+  if constexpr (NN < HI) return condense_dispatch<NN + 1, HI>(pl, evals, lay, prime_lo, nprimes, detvals, st);
   return POLYDET_EINVAL;
 }

@@ -7,7 +7,7 @@
 #define PD_CAT(a, b) PD_CAT2(a, b)
 
 int PD_CAT(pd_condense_from_, PD_N_LO)(const polydet_plan_s *pl, const uint32_t *evals,
-                                       int prime_lo, int nprimes, uint32_t *detvals,
+                                       EvLayout lay, int prime_lo, int nprimes, uint32_t *detvals,
                                        cudaStream_t st) {
-  return condense_dispatch<PD_N_LO, PD_N_HI>(pl, evals, prime_lo, nprimes, detvals, st);
+  return condense_dispatch<PD_N_LO, PD_N_HI>(pl, evals, lay, prime_lo, nprimes, detvals, st);
 }

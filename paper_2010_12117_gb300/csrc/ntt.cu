@@ -39,6 +39,8 @@ struct TxArgs {
   // e goes to ((r * (B / il_L) + b / il_L) * il_n2 + e) * il_Lp + b % il_L
   int il_L, il_Lp;
   int64_t il_n2;
+  // output row stride (words between rows r and r + 1 of a column); 0: B
+  int64_t out_row;
 };
 
 __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
@@ -116,7 +118,8 @@ __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
         a.out[(int64_t)blockIdx.z * a.out_prime_stride + (row * a.il_n2 + blockIdx.y) * a.il_Lp +
               bb % a.il_L] = v;
       } else {
-        a.out[out_base + (aa * a.Lout + r) * a.B + bb] = v;
+        const int64_t orow = a.out_row ? a.out_row : a.B;
+        a.out[out_base + (aa * a.Lout + r) * orow + bb] = v;
       }
     } else if (a.inverse && v != 0u) {
       bad = true;
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
   if (a.il_L)
     ostride = (a.B / a.il_L) * a.il_n2 * a.il_Lp;  // row r -> row index r * (B / L)
   else
-    ostride = a.B;
+    ostride = a.out_row ? a.out_row : a.B;
   uint32_t c[CPT][LIN];
   uint32_t *op[CPT];  // output row 0 of each column (null past the last column)
 #pragma unroll
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
               bb % a.il_L;
     else
       obase = (int64_t)blockIdx.z * a.out_prime_stride + (int64_t)blockIdx.y * a.out_item_stride +
-              aa * a.Lout * a.B + bb;
+              aa * a.Lout * ostride + bb;
     op[k] = ok ? a.out + obase : nullptr;
   }
   const uint32_t *tw = a.tw + (size_t)q * a.tw_len + a.tw_off;
@@ -613,19 +616,27 @@ int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, uint32_t *head
   return POLYDET_OK;
 }
 
+EvLayout pd_tail_layout(const polydet_plan_s *pl) {
+  const int64_t B = pl->G / pl->M[0];  // nodes of the other variables: one row
+  const int64_t Bs = B >= 64 ? (B + 31) / 32 * 32 : B;
+  return EvLayout{B, Bs, (int64_t)pl->M[0] * Bs};
+}
+
 int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int lo, int hi, uint32_t *evals,
-                 cudaStream_t st) {
+                 EvLayout lay, cudaStream_t st) {
   if (check_range(pl, lo, hi) || !head || !evals) return POLYDET_EINVAL;
   const int64_t n2 = (int64_t)pl->n * pl->n;
   const int64_t S1 = (int64_t)pd_head_words(pl);
   TxArgs a = forward_pass(pl, 0, lo);
+  if (lay.rowlen != a.B || lay.entry != (int64_t)pl->M[0] * lay.rowstride) return POLYDET_EINVAL;
   a.in = head + (int64_t)lo * n2 * S1;
   a.in_item_stride = S1;
   a.in_prime_stride = n2 * S1;
   a.in_is_i32 = 0;
   a.out = evals;
-  a.out_item_stride = pl->G;
-  a.out_prime_stride = n2 * pl->G;
+  a.out_row = lay.rowstride;
+  a.out_item_stride = lay.entry;
+  a.out_prime_stride = n2 * lay.entry;
   return launch_pass(a, (int)n2, hi - lo, st);
 }
 
@@ -701,5 +712,6 @@ int pd_eval_partial(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int
 extern "C" int polydet_condense_batch(polydet_plan_t pl, const uint32_t *evals, int lo, int hi,
                                       uint32_t *detvals, void *stream) {
   if (check_range(pl, lo, hi) || !evals || !detvals) return POLYDET_EINVAL;
-  return pd_launch_condense(pl, evals, lo, hi - lo, detvals, (cudaStream_t)stream);
+  const EvLayout lay = {pl->G, pl->G, pl->G};
+  return pd_launch_condense(pl, evals, lay, lo, hi - lo, detvals, (cudaStream_t)stream);
 }

@@ -17,7 +17,7 @@ import numpy as np
 import torch
 
 from .binding import (BATCH_FUSED, BATCH_MATERIALIZED, EBOUND, Plan, PolydetError, as_u32,
-                      limbs_to_ints)
+                      limbs_to_ints, tail_entry_words)
 from .pipeline import prime_count
 
 
@@ -243,7 +243,8 @@ class BatchedRunner:
             n, k, P, G = int(i.n), int(i.nvars), int(i.P), int(i.G)
             tot += max(1, k - 1)             # stage 1 passes (or the repack / reduction)
             if self.batch.mode(n) == BATCH_MATERIALIZED:
-                cp = max(1, min(P, int(self.batch.info.chunk_words) // (n * n * G)))
+                Gs = tail_entry_words(tuple(i.M[:k]))
+                cp = max(1, min(P, int(self.batch.info.chunk_words) // (n * n * Gs)))
                 tot += 2 * (-(-P // cp))     # first-variable pass + condensation per chunk
             tot += k + 1                     # interpolation passes and CRT
         fused = [n for n in self.batch.orders() if self.batch.mode(n) == BATCH_FUSED]
