@@ -19,6 +19,7 @@ import argparse
 import csv
 import io
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -285,9 +286,12 @@ def served_leg(args, mats, batched_value, st):
 
 
 def kernel_leg(st, hbm_peak):
-    """HBM-bound stages alone on inputs larger than L2: the eval NTT on the
-    12x12 trivariate grid (64^3 nodes, 5 primes: 755 MB written) and the CRT
-    on 2^24 coefficients with 6 and 11 primes."""
+    """Stages alone on inputs larger than L2 (the 12x12 trivariate workload):
+    evaluation on the node grid (37^3 nodes, 20 primes: 583 MB written) and on
+    the paper's full grid (64^3 nodes, 5 primes: 755 MB), interpolation on
+    both grids (inverse NTT on the full grid is HBM-bound; the node grid's
+    inverse Vandermonde is a dot product of 37 terms per output, integer-bound),
+    and the CRT on 2^24 coefficients with 6 and 11 primes."""
     import numpy as np
     import torch
     from paper_2010_12117_gb300 import synth
@@ -304,26 +308,35 @@ def kernel_leg(st, hbm_peak):
         e.synchronize()
         return s.elapsed_time(e) / reps
 
+    def hbm(ms, byts):
+        return {"ms": ms, "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak,
+                "algorithmic_bytes": byts, "bound": "hbm"}
+
     out = {}
     pm = synth.sparse_12x12_xyz(0)
-    P = 5
-    pl = Plan(pm.n, pm.degs, P)
     c = torch.from_numpy(pm.coeffs.astype(np.int32).reshape(-1)).cuda()
-    ev = torch.empty(P * pm.n * pm.n * pl.G, dtype=torch.int32, device="cuda")
-    ws = pl.workspace(P)
-    ms = timed(lambda: pl.eval(c, 0, P, ev, ws, st))
-    byts = 4.0 * P * pm.n * pm.n * (pl.E + pl.G)
-    out["eval_ntt_12x12_xyz"] = {"ms": ms, "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak,
-                                 "algorithmic_bytes": byts}
-    dv = torch.empty(P * pl.G, dtype=torch.int32, device="cuda")
-    pl.condense(ev, 0, P, dv, st)
-    rs = torch.empty(P * pl.C, dtype=torch.int32, device="cuda")
-    ms = timed(lambda: pl.interp(dv, 0, P, rs, ws, st))
-    byts = 4.0 * P * (pl.G + pl.C)
-    out["interp_ntt_12x12_xyz"] = {"ms": ms, "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak,
-                                   "algorithmic_bytes": byts}
-    pl.close()
-    del ev, ws, dv, rs
+    n2 = pm.n * pm.n
+    for name, P, full in (("node_grid_37^3_P20", 20, False), ("full_grid_64^3_P5", 5, True)):
+        pl = Plan(pm.n, pm.degs, P, full_grid=full)
+        ev = torch.empty(P * n2 * pl.G, dtype=torch.int32, device="cuda")
+        ws = pl.workspace(P)
+        ms = timed(lambda: pl.eval(c, 0, P, ev, ws, st))
+        out[f"eval_{name}"] = hbm(ms, 4.0 * P * n2 * (pl.E + pl.G))
+        dv = torch.empty(P * pl.G, dtype=torch.int32, device="cuda")
+        pl.condense(ev, 0, P, dv, st)
+        del ev
+        rs = torch.empty(P * pl.C, dtype=torch.int32, device="cuda")
+        ms = timed(lambda: pl.interp(dv, 0, P, rs, ws, st))
+        if full:
+            out[f"interp_{name}"] = hbm(ms, 4.0 * P * (pl.G + pl.C))
+        else:
+            macs = float(P) * sum(pl.M[v] * math.prod(pl.M[:v]) * math.prod(x + 1 for x in pl.D[v:])
+                                  for v in range(pl.k))
+            out[f"interp_{name}"] = {"ms": ms, "Gmac_per_s": macs / ms / 1e6, "bound": "alu",
+                                     "macs": macs, "GBps": 4.0 * P * (pl.G + pl.C) / ms / 1e6}
+        pl.close()
+        del dv, rs, ws
+        torch.cuda.empty_cache()
     for P in (6, 11):
         pc = Plan(1, (4095, 4095), P)  # C = 4096^2 = 2^24 coefficients
         C = pc.C
@@ -331,8 +344,7 @@ def kernel_leg(st, hbm_peak):
         limbs = torch.empty(C * pc.W, dtype=torch.int32, device="cuda")
         ms = timed(lambda: pc.crt(res, limbs, st))
         byts = 4.0 * C * (P + pc.W)
-        out[f"crt_2^24_P{P}"] = {"ms": ms, "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak,
-                                 "algorithmic_bytes": byts, "W": pc.W}
+        out[f"crt_2^24_P{P}"] = dict(hbm(ms, byts), W=pc.W)
         pc.close()
         del res, limbs
     torch.cuda.empty_cache()

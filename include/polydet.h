@@ -25,11 +25,16 @@
  * Grid and coefficient layouts (Sec. 2, dense encoding, x1 slowest):
  *  - entry coefficients: int32 [n][n][E], E = prod_v (d_v + 1), exponent
  *    vectors (e1..ek) with 0 <= e_v <= d_v in lex order;
- *  - evaluation nodes: G = prod_v M_v nodes, node (i1..ik) is
- *    x_v = w_v^(i_v), 0 <= i_v < M_v, with w_v = g^((p-1)/N_v) for the least
- *    generator g of (Z/pZ)^*, N_v = nextpow2(D_v + 1), D_v = n * d_v, and
- *    M_v = D_v + 1 (node grid, default) or N_v (POLYDET_FLAG_FULL_GRID);
- *    flat index lex (i1 slowest);
+ *  - evaluation nodes: G = prod_v M_v nodes, node (k1..kk) with
+ *    0 <= k_v < M_v is x_v = w_v^(s_v(k_v)), with w_v = g^((p-1)/N_v) for
+ *    the least generator g of (Z/pZ)^*, N_v = nextpow2(D_v + 1),
+ *    D_v = n * d_v, M_v = D_v + 1 (node grid, default) or N_v
+ *    (POLYDET_FLAG_FULL_GRID); flat index lex (k1 slowest).  Full grid:
+ *    s_v(k) = k.  Node grid: coset order s_v(k) = k / L + (N_v / L) (k mod L)
+ *    with L = the smallest power of two >= min(d_v + 1, 8), so that the
+ *    first M_v nodes are whole cosets of the subgroup of L-th roots (one
+ *    register DFT of size L evaluates a coset; at most L - 1 nodes are
+ *    computed beyond M_v).  polydet_plan_nodes returns s_v;
  *  - determinant coefficients: C = prod_v (D_v + 1), lex over e_v <= D_v.
  */
 #ifndef POLYDET_H
@@ -83,9 +88,10 @@ typedef struct polydet_plan_info {
 
 /* Plan flag: evaluate on the full power-of-two grid (N_v nodes per variable)
  * and interpolate by inverse NTT, as the paper does (Sec. 3.1, 3.3).  Without
- * it the plan evaluates on the node grid: the first D_v + 1 powers of w_v,
- * i.e. exactly as many nodes as the degree bound needs (Sec. 2), and
- * interpolates with the inverse of their Vandermonde matrix.  Both give the
+ * it the plan evaluates on the node grid: D_v + 1 distinct powers of w_v
+ * (the first D_v + 1 in coset order), i.e. exactly as many nodes as the
+ * degree bound needs (Sec. 2), and interpolates with the inverse of their
+ * Vandermonde matrix.  Both give the
  * same determinant; the node grid condenses prod (D_v+1) / prod N_v as many
  * matrices. */
 #define POLYDET_FLAG_FULL_GRID 0x1u
@@ -119,6 +125,9 @@ int polydet_plan_query(polydet_plan_t plan, polydet_plan_info *info);
 /* Host copies: primes [P]; roots w_{q,v} as [P][nvars]. */
 int polydet_plan_primes(polydet_plan_t plan, uint32_t *primes_out);
 int polydet_plan_roots(polydet_plan_t plan, uint32_t *roots_out);
+/* Host copy of the node exponents of variable v: exps_out[k] = s_v(k) for
+ * k < M_v (node k of x_v is w_v^(s_v(k))). */
+int polydet_plan_nodes(polydet_plan_t plan, int var, int32_t *exps_out);
 
 /* Stage 1, evaluation (Sec. 3.1, Algorithm 2): for every prime q in
  * [prime_lo, prime_hi) and entry e, the multivariate NTT of the zero-padded

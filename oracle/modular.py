@@ -16,7 +16,7 @@ from __future__ import annotations
 
 from itertools import product
 from math import prod
-from typing import Dict, List, Sequence, Tuple
+from typing import Optional, Dict, List, Sequence, Tuple
 
 _MR_BASES = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
 
@@ -191,17 +191,19 @@ def solve_mod_p(A: Sequence[Sequence[int]], b: Sequence[int], p: int) -> List[in
 
 
 def interp_nodes(values: Sequence[int], Ms: Sequence[int], omegas: Sequence[int],
-                 p: int) -> List[int]:
-    """Interpolation through the node grid x_v = omega_v^i, 0 <= i < M_v
-    (Sec. 3.3: unique polynomial of degree < M_v in each variable through
-    those nodes): one Vandermonde system V c = y per line, variable by
-    variable.  ``values`` lex over the grid; returns lex coefficients of the
-    box prod [0, M_v)."""
+                 p: int, exps: Optional[Sequence[Sequence[int]]] = None) -> List[int]:
+    """Interpolation through the node grid x_v = omega_v^(s_v(i)), 0 <= i < M_v,
+    with s_v(i) = i unless ``exps[v]`` lists the exponents s_v (any M_v
+    distinct powers; Sec. 3.3: the polynomial of degree < M_v in each variable
+    through M_v distinct nodes is unique): one Vandermonde system V c = y per
+    line, variable by variable.  ``values`` lex over the grid; returns lex
+    coefficients of the box prod [0, M_v)."""
     k = len(Ms)
     cur = [int(v) % p for v in values]
     for v in range(k - 1, -1, -1):
         m = Ms[v]
-        V = [[pow(omegas[v], i * e, p) for e in range(m)] for i in range(m)]
+        s = list(range(m)) if exps is None else [int(x) for x in exps[v]]
+        V = [[pow(omegas[v], s[i] * e, p) for e in range(m)] for i in range(m)]
         inner = prod(Ms[v + 1:])
         outer = prod(Ms[:v])
         nxt = [0] * len(cur)

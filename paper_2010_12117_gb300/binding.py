@@ -82,6 +82,7 @@ SIGNATURES = {
     "polydet_plan_query": (_I, [_VP, ctypes.POINTER(PlanInfo)]),
     "polydet_plan_primes": (_I, [_VP, _PU32]),
     "polydet_plan_roots": (_I, [_VP, _PU32]),
+    "polydet_plan_nodes": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_int32)]),
     "polydet_eval": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP]),
     "polydet_condense_batch": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
     "polydet_interp": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP]),
@@ -206,6 +207,11 @@ class Plan:
         rt = (ctypes.c_uint32 * (self.P * self.k))()
         _check(L.polydet_plan_roots(h, rt), "polydet_plan_roots")
         self.roots = [list(rt[q * self.k:(q + 1) * self.k]) for q in range(self.P)]
+        self.node_exps = []  # node k of x_v is root_v ** node_exps[v][k]
+        for v in range(self.k):
+            ex = (ctypes.c_int32 * max(1, self.M[v]))()
+            _check(L.polydet_plan_nodes(h, v, ex), "polydet_plan_nodes")
+            self.node_exps.append(list(ex[:self.M[v]]))
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -176,6 +176,7 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
       s.Mk = pl->M[k - 1];
       s.L = pl->d[k - 1] + 1;
       s.Lp = b->Lp[j];
+      s.LPk = pl->LPo[k - 1];
       b->segs[pl->n].push_back(s);
     }
   }

@@ -105,6 +105,7 @@ struct polydet_plan_s {
   // nodes per variable: D_v + 1 (node grid: the first D_v + 1 powers of w_v)
   // or N_v (full grid, POLYDET_FLAG_FULL_GRID); G = prod_v M_v
   int M[POLYDET_MAX_VARS];
+  int LPo[POLYDET_MAX_VARS];  // node order: node k is w^(k / LPo + (N / LPo)(k mod LPo))
   int full;                        // 1: full power-of-two grid + inverse NTT
   int vinv_off[POLYDET_MAX_VARS];  // node grid: offset of variable v's table
   int vinv_len;                    // node grid: sum_v M_v^2 words per prime
@@ -190,6 +191,7 @@ struct FusedSeg {
   int32_t logNk;       // log2 N_k (twiddle table of the last variable)
   int32_t Mk;          // nodes of the last variable (M_k): node g = row * Mk + i
   int32_t L, Lp;       // coefficients of x_k per entry, stride of the partial tensor
+  int32_t LPk;         // node order radix of the last variable (node_exp)
 };
 
 int pd_fused_launch(int n, const FusedSeg *segs, int nsegs, int64_t nitems, const uint32_t *partial,
@@ -198,6 +200,15 @@ int pd_fused_launch(int n, const FusedSeg *segs, int nsegs, int64_t nitems, cons
 // qwords: words of partial-tensor rows one CTA stages (rows per item x n^2 x Lp)
 int pd_fused_occupancy(int n, int threads, size_t qwords, int *blocks_per_sm);
 int pd_fused_team(int n);
+
+// Node exponent of node k of a variable with N points and order radix L
+// (L = 1: natural order): cosets of the L-th roots, one after another.
+PD_HD int node_exp(int k, int N, int L) { return k / L + (N / L) * (k % L); }
+// Order radix of a variable of entry degree d on the node grid.
+PD_HD int node_radix(int d) {
+  const int lin = d + 1 < 8 ? d + 1 : 8;
+  return lin <= 1 ? 1 : lin <= 2 ? 2 : lin <= 4 ? 4 : 8;
+}
 
 // Lanes per matrix (T) and the resident CTAs of 128 threads the condensation
 // kernel of each order n is compiled for (its __launch_bounds__ minimum),

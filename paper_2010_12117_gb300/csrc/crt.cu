@@ -84,7 +84,25 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
                                                     const uint32_t *__restrict__ mfull) {
   __shared__ uint32_t gs[PT * PT];
   __shared__ uint32_t ps[PT], pis[PT], mh[PT], mf[PT];
-  for (int i = threadIdx.x; i < PT * PT; i += blockDim.x) gs[i] = garner[i];
+  // per warp: its 32 coefficients' limbs, written out as one contiguous run
+  // (coefficients c .. c + 31 own words [c W, (c + 32) W) of the output)
+  __shared__ uint32_t stage[256 / 32][32 * PT];
+  // gs[i][j] (j < i) = -G_ij G_ii and gs[i][i] = G_ii (Montgomery forms), so
+  // that alpha_i = x_i G_ii + sum_{j<i} alpha_j (-G_ij G_ii) is one dot
+  // product mod p_i (the Garner step of Sec. 3.4 with its subtraction and
+  // final scaling folded into the constants)
+  for (int f = threadIdx.x; f < PT * PT; f += blockDim.x) {
+    const int i = f / PT, j = f - i * PT;
+    const ModP md = mod[i];
+    uint32_t v = 0u;
+    if (j == i) {
+      v = garner[f];
+    } else if (j < i) {
+      const uint32_t t = mmul(garner[f], garner[i * PT + i], md.p, md.pinv);
+      v = t ? md.p - t : 0u;
+    }
+    gs[f] = v;
+  }
   for (int i = threadIdx.x; i < PT; i += blockDim.x) {
     ps[i] = mod[i].p;
     pis[i] = mod[i].pinv;
@@ -92,8 +110,11 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
     mf[i] = i < W ? mfull[i] : 0u;
   }
   __syncthreads();
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *sw = stage[warp];
+  for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < C;
+       c0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = c0 + lane < C ? c0 + lane : C - 1;  // the warp stays whole
     uint32_t x[PT], al[PT];
 #pragma unroll
     for (int i = 0; i < PT; ++i) x[i] = __ldg(res + (int64_t)i * C + c);
@@ -101,10 +122,16 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
 #pragma unroll
     for (int i = 1; i < PT; ++i) {
       const uint32_t p = ps[i], pinv = pis[i];
+      // terms j <= i: (alpha_j or x_i) * gs[i][j]; two 62-bit products
+      // (each below 2^31 p_i) share one REDC
       uint32_t acc = 0u;
 #pragma unroll
-      for (int j = 0; j < i; ++j) acc = addm(acc, mmul(al[j], gs[i * PT + j], p, pinv), p);
-      al[i] = mmul(subm(x[i], acc, p), gs[i * PT + i], p, pinv);
+      for (int j = 0; j <= i; j += 2) {
+        uint64_t sum = (uint64_t)(j < i ? al[j] : x[i]) * gs[i * PT + j];
+        if (j + 1 <= i) sum += (uint64_t)(j + 1 < i ? al[j + 1] : x[i]) * gs[i * PT + j + 1];
+        acc = (j == 0) ? redc(sum, p, pinv) : addm(acc, redc(sum, p, pinv), p);
+      }
+      al[i] = acc;
     }
     uint32_t X[PT];
 #pragma unroll
@@ -134,10 +161,14 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
         borrow = (uint32_t)(t >> 63);
       }
     }
-    uint32_t *o = limbs + c * W;
 #pragma unroll
     for (int w = 0; w < PT; ++w)
-      if (w < W) o[w] = X[w];
+      if (w < W) sw[lane * W + w] = X[w];
+    __syncwarp();
+    const int64_t nw = (C - c0 < 32 ? C - c0 : 32) * W;  // words of this warp's coefficients
+    uint32_t *o = limbs + c0 * W;
+    for (int f = lane; f < nw; f += 32) o[f] = sw[f];
+    __syncwarp();
   }
 }
 

@@ -41,6 +41,9 @@ struct TxArgs {
   int64_t il_n2;
   // output row stride (words between rows r and r + 1 of a column); 0: B
   int64_t out_row;
+  // node order of the output rows (forward passes): row k holds the value at
+  // w^node_exp(k, N, olp); 0 or 1: natural order
+  int olp;
 };
 
 __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
@@ -110,16 +113,21 @@ __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
     const int64_t col = col0 + c;
     if (col >= ncols) continue;
     uint32_t v = sm[r * S + c];
-    if (r < a.Lout) {
+    // natural output index r -> its row in the node order (r = j + (N/L) t
+    // is node j L + t)
+    const int L = a.olp > 1 ? a.olp : 1;
+    const int J = N / L;
+    const int rk = (r % J) * L + r / J;
+    if (rk < a.Lout) {
       if (a.inverse) v = mmul(scale, v, md.p, md.pinv);
       const int64_t aa = col / a.B, bb = col - aa * a.B;
       if (a.il_L) {
-        const int64_t row = (int64_t)r * (a.B / a.il_L) + bb / a.il_L;
+        const int64_t row = (int64_t)rk * (a.B / a.il_L) + bb / a.il_L;
         a.out[(int64_t)blockIdx.z * a.out_prime_stride + (row * a.il_n2 + blockIdx.y) * a.il_Lp +
               bb % a.il_L] = v;
       } else {
         const int64_t orow = a.out_row ? a.out_row : a.B;
-        a.out[out_base + (aa * a.Lout + r) * orow + bb] = v;
+        a.out[out_base + (aa * a.Lout + rk) * orow + bb] = v;
       }
     } else if (a.inverse && v != 0u) {
       bad = true;
@@ -221,16 +229,20 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
     psi2 = r4;
     psi3 = __ldg(tw + 3 * (N >> 3));
   }
-  // rows j + J t < Lout are stored: t < tfull always, t >= tfull while j < lim[t]
+  // Natural order (olp <= 1): coset j holds rows j + J t, stored while
+  // j < lim[t].  Coset order (olp == LP): coset j holds rows j LP + t, so
+  // only the first ceil(Lout / LP) cosets are computed.
+  const bool coset_rows = a.olp > 1;
+  const int Jc = coset_rows ? (a.Lout + LP - 1) / LP : J;
   int lim[LP];
 #pragma unroll
-  for (int t = 0; t < LP; ++t) lim[t] = a.Lout - J * t;
-  for (int j = 0; j < J; ++j) {
+  for (int t = 0; t < LP; ++t) lim[t] = coset_rows ? a.Lout - t : a.Lout - J * t;
+  for (int j = 0; j < Jc; ++j) {
     uint32_t w[LIN];
     w[0] = md.r1;
 #pragma unroll
     for (int e = 1; e < LIN; ++e) w[e] = tw_pow(tw, j * e, N, p);
-    const int64_t jo = (int64_t)j * ostride;
+    const int64_t jo = (int64_t)j * (coset_rows ? LP : 1) * ostride;
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
       uint32_t z[LP];
@@ -269,9 +281,10 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
       }
       if (op[k]) {
         uint32_t *o = op[k] + jo;
+        const int jr = coset_rows ? j * LP : j;  // compared with lim[t]
 #pragma unroll
         for (int t = 0; t < LP; ++t)
-          if (j < lim[t]) o[(int64_t)(J * t) * ostride] = y[t];
+          if (jr < lim[t]) o[(int64_t)(coset_rows ? t : J * t) * ostride] = y[t];
       }
     }
   }
@@ -286,7 +299,8 @@ static int ilog2(int64_t x) {
 static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
   int64_t ncols = a.A * a.B;
   // short forward transforms over many columns: the register-direct kernel
-  if (!a.inverse && a.Lin <= 8 && a.B >= 8) {
+  const int lp_in = a.Lin <= 1 ? 1 : a.Lin <= 2 ? 2 : a.Lin <= 4 ? 4 : 8;
+  if (!a.inverse && a.Lin <= 8 && a.B >= 8 && (a.olp <= 1 || a.olp == lp_in)) {
     constexpr int CPT = 4;
     dim3 grid((unsigned)((ncols + 256 * CPT - 1) / (256 * CPT)), (unsigned)items, (unsigned)nprimes);
     switch (a.Lin) {
@@ -344,7 +358,8 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
     a.Lin = pl->d[v] + 1;
     a.N = pl->N[v];
     a.logN = pl->logN[v];
-    a.Lout = pl->M[v];  // the first M_v outputs of the N_v-point transform
+    a.Lout = pl->M[v];  // the first M_v nodes (in the plan's order) of the N_v-point transform
+    a.olp = pl->LPo[v];
     a.in = cur_in;
     a.in_item_stride = cur_item;
     a.in_prime_stride = cur_prime;
@@ -567,6 +582,7 @@ static TxArgs forward_pass(const polydet_plan_s *pl, int v, int lo) {
   a.N = pl->N[v];
   a.logN = pl->logN[v];
   a.Lout = pl->M[v];
+  a.olp = pl->LPo[v];
   a.inverse = 0;
   a.prime_lo = lo;
   a.mod = pl->d_mod;
@@ -675,6 +691,7 @@ int pd_eval_partial(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int
     a.N = pl->N[v];
     a.logN = pl->logN[v];
     a.Lout = pl->M[v];
+    a.olp = pl->LPo[v];
     a.in = cur_in;
     a.in_item_stride = cur_item;
     a.in_prime_stride = cur_prime;

@@ -202,6 +202,7 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
     pl->logN[v] = lg;
     pl->E *= (int64_t)(pl->d[v] + 1);
     pl->M[v] = (flags & POLYDET_FLAG_FULL_GRID) ? pl->N[v] : pl->D[v] + 1;
+    pl->LPo[v] = (flags & POLYDET_FLAG_FULL_GRID) ? 1 : node_radix(pl->d[v]);
     pl->G *= pl->M[v];
     pl->C *= (int64_t)(pl->D[v] + 1);
     pl->tw_off[v] = off;
@@ -314,8 +315,8 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
         uint32_t *dst0 = vinv.data() + (size_t)q * off2 + pl->vinv_off[v];
         // tables depend on (p, w, m) only: compute each once per process
         static std::mutex vmu;
-        static std::map<std::tuple<uint32_t, uint32_t, int>, std::vector<uint32_t>> vcache;
-        const auto key = std::make_tuple((uint32_t)p, pl->roots[q][v], m);
+        static std::map<std::tuple<uint32_t, uint32_t, int, int>, std::vector<uint32_t>> vcache;
+        const auto key = std::make_tuple((uint32_t)p, pl->roots[q][v], m, pl->LPo[v]);
         {
           std::lock_guard<std::mutex> lock(vmu);
           auto it = vcache.find(key);
@@ -325,11 +326,8 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
           }
         }
         std::vector<uint64_t> x(m), mc(m + 1, 0), qc(m);
-        uint64_t w = 1;
-        for (int i = 0; i < m; ++i) {
-          x[i] = w;
-          w = w * pl->roots[q][v] % p;
-        }
+        for (int i = 0; i < m; ++i)  // the nodes in the plan's order
+          x[i] = h_powmod(pl->roots[q][v], (uint64_t)node_exp(i, pl->N[v], pl->LPo[v]), (uint32_t)p);
         mc[0] = 1;  // m(x), built factor by factor; mc[k] = coefficient of x^k
         for (int j = 0; j < m; ++j) {
           for (int k = j + 1; k >= 1; --k) mc[k] = (mc[k - 1] + (p - x[j]) * mc[k]) % p;
@@ -405,6 +403,12 @@ extern "C" int polydet_plan_roots(polydet_plan_t pl, uint32_t *roots_out) {
   if (!pl || !roots_out) return POLYDET_EINVAL;
   for (int q = 0; q < pl->P; ++q)
     for (int v = 0; v < pl->nvars; ++v) roots_out[q * pl->nvars + v] = pl->roots[q][v];
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_plan_nodes(polydet_plan_t pl, int var, int32_t *exps_out) {
+  if (!pl || !exps_out || var < 0 || var >= pl->nvars) return POLYDET_EINVAL;
+  for (int k = 0; k < pl->M[var]; ++k) exps_out[k] = node_exp(k, pl->N[var], pl->LPo[var]);
   return POLYDET_OK;
 }
 

@@ -76,7 +76,8 @@ def test_eval_matches_direct_evaluation(n, degs, P, sample, full):
             vec = pm.coeffs.reshape(n * n, -1)[e].tolist()
             for g in nodes:
                 idx = modular.grid_index(g, pl.M)
-                assert int(got[q, e, g]) == modular.eval_point(vec, degs, idx, ws, p), (q, e, g)
+                ex = [pl.node_exps[v][i] for v, i in enumerate(idx)]  # the plan's node order
+                assert int(got[q, e, g]) == modular.eval_point(vec, degs, ex, ws, p), (q, e, g)
 
 
 def test_eval_prime_range_offsets():
@@ -171,7 +172,9 @@ def test_interp_round_trip_against_oracle(full, degs):
         p = pl.primes[q]
         vec = [rng.randrange(p) for _ in range(pl.C)]
         want.append(vec)
-        det_vals[q] = modular.eval_grid(vec, pl.D, pl.M, pl.roots[q], p)
+        det_vals[q] = [modular.eval_point(vec, pl.D, [pl.node_exps[v][i] for v, i in
+                                                      enumerate(modular.grid_index(g, pl.M))],
+                                          pl.roots[q], p) for g in range(pl.G)]
     dv = torch.from_numpy(det_vals.astype(np.uint32).view(np.int32).reshape(-1)).cuda()
     res = torch.empty(P * pl.C, dtype=torch.int32, device="cuda")
     pl.interp(dv, 0, P, res, pl.workspace(P))
@@ -184,7 +187,26 @@ def test_interp_round_trip_against_oracle(full, degs):
         box, clean = modular.interp_grid(det_vals[0].tolist(), pl.N, pl.roots[0], pl.primes[0], pl.D)
         assert clean and box == want[0]
     else:
-        assert modular.interp_nodes(det_vals[0].tolist(), pl.M, pl.roots[0], pl.primes[0]) == want[0]
+        assert modular.interp_nodes(det_vals[0].tolist(), pl.M, pl.roots[0], pl.primes[0],
+                                    pl.node_exps) == want[0]
+
+
+@pytest.mark.parametrize("n,degs", [(4, (1, 2, 3)), (24, (3, 4)), (1, (7,)), (3, (0, 2))])
+def test_node_order_is_whole_cosets(n, degs):
+    """The node grid visits distinct powers of w_v coset by coset: node k is
+    w^(k // L + (N/L) (k mod L)) with L = pow2 >= min(d_v + 1, 8); the full
+    grid is natural."""
+    pl = Plan(n, degs, 2)
+    for v, d in enumerate(degs):
+        L = 1
+        while L < min(d + 1, 8):
+            L *= 2
+        N = pl.N[v]
+        want = [k // L + (N // L) * (k % L) for k in range(pl.M[v])]
+        assert pl.node_exps[v] == want
+        assert len(set(want)) == pl.M[v] and max(want) < N
+    full = Plan(n, degs, 2, full_grid=True)
+    assert full.node_exps == [list(range(N)) for N in full.N]
 
 
 def test_interp_flags_a_degree_bound_violation():

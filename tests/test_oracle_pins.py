@@ -421,3 +421,22 @@ def test_workload_generators_shapes():
     assert all(4 <= m.n <= 24 and 1 <= m.nvars <= 3 and all(1 <= d <= 4 for d in m.degs) for m in b)
     # the same seed gives the same input
     assert np.array_equal(synth.sparse_12x12_xyz(3).coeffs, synth.sparse_12x12_xyz(3).coeffs)
+
+
+def test_node_grid_interpolation_on_coset_ordered_nodes():
+    """Interpolation through nodes in coset order (node k = omega^(k // L +
+    (N / L)(k mod L)), the library's node grid) returns the coefficients, and
+    with the nodes misdeclared as the natural powers it does not."""
+    rng = random.Random(13)
+    p = PRIMES[5]
+    D = (4, 5)
+    Ms = tuple(d + 1 for d in D)
+    Ns = plan.grid_sizes(D)
+    ws = [modular.root_of_unity(p, N) for N in Ns]
+    Ls = (4, 2)
+    exps = [[k // L + (N // L) * (k % L) for k in range(M)] for M, N, L in zip(Ms, Ns, Ls)]
+    vec = [rng.randrange(p) for _ in range(prod(Ms))]
+    vals = [modular.eval_point(vec, D, [exps[v][i] for v, i in enumerate(modular.grid_index(g, Ms))], ws, p)
+            for g in range(prod(Ms))]
+    assert modular.interp_nodes(vals, Ms, ws, p, exps) == vec
+    assert modular.interp_nodes(vals, Ms, ws, p) != vec
