@@ -291,11 +291,11 @@ class Plan:
 def tail_entry_words(M) -> int:
     """Words per entry of a materialized chunk for node counts M (per
     variable): rows of the first variable padded to 32 words when they hold
-    at least 64 nodes (the library's layout of the chunk)."""
+    at least 1024 nodes (the library's layout of the chunk)."""
     B = 1
     for m in M[1:]:
         B *= int(m)
-    Bs = -(-B // 32) * 32 if B >= 64 else B
+    Bs = -(-B // 32) * 32 if B >= 1024 else B
     return int(M[0]) * Bs
 
 

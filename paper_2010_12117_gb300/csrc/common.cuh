@@ -175,7 +175,8 @@ int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, uint32_t *head
 int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int lo, int hi, uint32_t *evals,
                  EvLayout lay, cudaStream_t st);
 // The tail's layout: rows of the first variable padded to 32 words when a
-// row holds at least 64 nodes (aligned rows store at full bandwidth).
+// row holds at least 1024 nodes (aligned rows store at full bandwidth; on
+// shorter rows the padding would cost more read traffic than it saves).
 EvLayout pd_tail_layout(const polydet_plan_s *pl);
 
 // One (job, prime) pair of a fused launch: the nodes [0, G) of that job and

@@ -634,7 +634,7 @@ int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, uint32_t *head
 
 EvLayout pd_tail_layout(const polydet_plan_s *pl) {
   const int64_t B = pl->G / pl->M[0];  // nodes of the other variables: one row
-  const int64_t Bs = B >= 64 ? (B + 31) / 32 * 32 : B;
+  const int64_t Bs = B >= 1024 ? (B + 31) / 32 * 32 : B;  // padding <= 3 % of a row
   return EvLayout{B, Bs, (int64_t)pl->M[0] * Bs};
 }
 
