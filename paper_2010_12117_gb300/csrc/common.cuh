@@ -110,7 +110,7 @@ struct polydet_plan_s {
   int vinv_off[POLYDET_MAX_VARS];  // node grid: offset of variable v's table
   int vinv_len;                    // node grid: sum_v M_v^2 words per prime
   uint32_t *d_vinv;                // [P][vinv_len] inverse Vandermonde * R
-  int tw_len;                      // sum_v N_v / 2: twiddles per prime
+  int tw_len;                      // sum_v N_v: twiddles per prime
   uint32_t primes[POLYDET_MAX_PRIMES];
   uint32_t roots[POLYDET_MAX_PRIMES][POLYDET_MAX_VARS];
   ModP mod_h[POLYDET_MAX_PRIMES];   // host copies of the per-prime constants
@@ -186,7 +186,7 @@ struct FusedSeg {
   int64_t G;           // grid nodes
   int64_t q_off;       // words into the partial tensor (or the int32 coefficients)
   int64_t det_off;     // words into the determinant values
-  const uint32_t *tw;  // w_k^j * R for j < N_k / 2 (last variable, this prime)
+  const uint32_t *tw;  // w_k^j * R for j < N_k (last variable, this prime)
   ModP md;
   uint32_t rn;         // R^n mod p
   int32_t logNk;       // log2 N_k (twiddle table of the last variable)

@@ -112,12 +112,24 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *sw = stage[warp];
-  for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); c0 < C;
-       c0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = c0 + lane < C ? c0 + lane : C - 1;  // the warp stays whole
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // residues of the next coefficient are loaded while this one is computed
+  uint32_t xn[PT];
+  int64_t c0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  if (c0 < C) {
+    const int64_t c = c0 + lane < C ? c0 + lane : C - 1;
+#pragma unroll
+    for (int i = 0; i < PT; ++i) xn[i] = __ldg(res + (int64_t)i * C + c);
+  }
+  for (; c0 < C; c0 += stride) {
     uint32_t x[PT], al[PT];
 #pragma unroll
-    for (int i = 0; i < PT; ++i) x[i] = __ldg(res + (int64_t)i * C + c);
+    for (int i = 0; i < PT; ++i) x[i] = xn[i];
+    if (c0 + stride < C) {
+      const int64_t c = c0 + stride + lane < C ? c0 + stride + lane : C - 1;  // the warp stays whole
+#pragma unroll
+      for (int i = 0; i < PT; ++i) xn[i] = __ldg(res + (int64_t)i * C + c);
+    }
     al[0] = x[0];
 #pragma unroll
     for (int i = 1; i < PT; ++i) {

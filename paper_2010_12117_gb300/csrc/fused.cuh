@@ -198,9 +198,8 @@ __global__ void __launch_bounds__(128) fused_kernel(const FusedSeg *__restrict__
     if (logNk == 0) {
       X[1] = sg.md.r1;
     } else {
-      const int h = 1 << (logNk - 1);
       const int ex = node_exp(ik, 1 << logNk, sg.LPk);  // node ik of x_k is w^ex
-      X[1] = (ex < h) ? __ldg(sg.tw + ex) : p - __ldg(sg.tw + (ex - h));
+      X[1] = __ldg(sg.tw + ex);
     }
 #pragma unroll
     for (int l = 2; l < 8; ++l) X[l] = (l < L) ? mmul(X[l - 1], X[1], p, pinv) : 0u;

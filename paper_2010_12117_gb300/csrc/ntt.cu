@@ -144,9 +144,8 @@ __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
 // the LP - Lin inputs that are zero are folded away at compile time.  A
 // thread owns CPT columns (blockDim apart, so every store of a row stays
 // coalesced) and loads each coset's twiddles once for all of them.
-__device__ __forceinline__ uint32_t tw_pow(const uint32_t *tw, int k, int N, uint32_t p) {
-  const int h = N >> 1;  // w^(k) for 0 <= k < N from the table of w^j, j < N/2
-  return k < h ? __ldg(tw + k) : p - __ldg(tw + (k - h));
+__device__ __forceinline__ uint32_t tw_pow(const uint32_t *tw, int k) {
+  return __ldg(tw + k);  // w^k * R for 0 <= k < N: the table holds the whole circle
 }
 
 // x + y and x - y mod p where ZX / ZY say that x / y is known to be zero.
@@ -235,14 +234,19 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
   const bool coset_rows = a.olp > 1;
   const int Jc = coset_rows ? (a.Lout + LP - 1) / LP : J;
   int lim[LP];
+  int64_t toff[LP];  // words from a coset's first row to its row t
 #pragma unroll
-  for (int t = 0; t < LP; ++t) lim[t] = coset_rows ? a.Lout - t : a.Lout - J * t;
+  for (int t = 0; t < LP; ++t) {
+    lim[t] = coset_rows ? a.Lout - t : a.Lout - J * t;
+    toff[t] = (int64_t)(coset_rows ? t : J * t) * ostride;
+  }
+  const int64_t jstep = (int64_t)(coset_rows ? LP : 1) * ostride;  // next coset's first row
   for (int j = 0; j < Jc; ++j) {
     uint32_t w[LIN];
     w[0] = md.r1;
 #pragma unroll
-    for (int e = 1; e < LIN; ++e) w[e] = tw_pow(tw, j * e, N, p);
-    const int64_t jo = (int64_t)j * (coset_rows ? LP : 1) * ostride;
+    for (int e = 1; e < LIN; ++e) w[e] = tw_pow(tw, j * e);
+
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
       uint32_t z[LP];
@@ -280,11 +284,11 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
         y[7] = subm(E[3], t3, p);
       }
       if (op[k]) {
-        uint32_t *o = op[k] + jo;
         const int jr = coset_rows ? j * LP : j;  // compared with lim[t]
 #pragma unroll
         for (int t = 0; t < LP; ++t)
-          if (jr < lim[t]) o[(int64_t)(coset_rows ? t : J * t) * ostride] = y[t];
+          if (jr < lim[t]) op[k][toff[t]] = y[t];
+        op[k] += jstep;
       }
     }
   }
@@ -296,25 +300,36 @@ static int ilog2(int64_t x) {
   return l;
 }
 
+template <int CPT>
+static int launch_direct(const TxArgs &a, int64_t ncols, int items, int nprimes, cudaStream_t st) {
+  dim3 grid((unsigned)((ncols + 256 * CPT - 1) / (256 * CPT)), (unsigned)items, (unsigned)nprimes);
+  switch (a.Lin) {
+    case 1: coltx_direct_kernel<1, CPT><<<grid, 256, 0, st>>>(a); break;
+    case 2: coltx_direct_kernel<2, CPT><<<grid, 256, 0, st>>>(a); break;
+    case 3: coltx_direct_kernel<3, CPT><<<grid, 256, 0, st>>>(a); break;
+    case 4: coltx_direct_kernel<4, CPT><<<grid, 256, 0, st>>>(a); break;
+    case 5: coltx_direct_kernel<5, CPT><<<grid, 256, 0, st>>>(a); break;
+    case 6: coltx_direct_kernel<6, CPT><<<grid, 256, 0, st>>>(a); break;
+    case 7: coltx_direct_kernel<7, CPT><<<grid, 256, 0, st>>>(a); break;
+    default: coltx_direct_kernel<8, CPT><<<grid, 256, 0, st>>>(a); break;
+  }
+  PD_CUDA(cudaGetLastError());
+  return POLYDET_OK;
+}
+
 static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
   int64_t ncols = a.A * a.B;
   // short forward transforms over many columns: the register-direct kernel
   const int lp_in = a.Lin <= 1 ? 1 : a.Lin <= 2 ? 2 : a.Lin <= 4 ? 4 : 8;
   if (!a.inverse && a.Lin <= 8 && a.B >= 8 && (a.olp <= 1 || a.olp == lp_in)) {
-    constexpr int CPT = 4;
-    dim3 grid((unsigned)((ncols + 256 * CPT - 1) / (256 * CPT)), (unsigned)items, (unsigned)nprimes);
-    switch (a.Lin) {
-      case 1: coltx_direct_kernel<1, CPT><<<grid, 256, 0, st>>>(a); break;
-      case 2: coltx_direct_kernel<2, CPT><<<grid, 256, 0, st>>>(a); break;
-      case 3: coltx_direct_kernel<3, CPT><<<grid, 256, 0, st>>>(a); break;
-      case 4: coltx_direct_kernel<4, CPT><<<grid, 256, 0, st>>>(a); break;
-      case 5: coltx_direct_kernel<5, CPT><<<grid, 256, 0, st>>>(a); break;
-      case 6: coltx_direct_kernel<6, CPT><<<grid, 256, 0, st>>>(a); break;
-      case 7: coltx_direct_kernel<7, CPT><<<grid, 256, 0, st>>>(a); break;
-      default: coltx_direct_kernel<8, CPT><<<grid, 256, 0, st>>>(a); break;
+    // columns per thread: more share each coset's twiddles, fewer leave
+    // fewer idle lanes in the last CTA of a row of B columns
+    const int cpt = ncols >= 8192 ? 4 : (ncols >= 2048 ? 2 : 1);
+    switch (cpt) {
+      case 4: return launch_direct<4>(a, ncols, items, nprimes, st);
+      case 2: return launch_direct<2>(a, ncols, items, nprimes, st);
+      default: return launch_direct<1>(a, ncols, items, nprimes, st);
     }
-    PD_CUDA(cudaGetLastError());
-    return POLYDET_OK;
   }
   // Ct: columns per CTA, a power of two with N * (Ct + 1) words <= 64 KB.
   int ct = 32;

@@ -206,7 +206,7 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
     pl->G *= pl->M[v];
     pl->C *= (int64_t)(pl->D[v] + 1);
     pl->tw_off[v] = off;
-    off += (pl->N[v] + 1) / 2;
+    off += pl->N[v];  // the whole circle: a twiddle is one load, no sign flip
   }
   pl->tw_len = off > 0 ? off : 1;
 
@@ -230,7 +230,7 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
       uint32_t wi = h_powmod(w, p - 2, p);
       pl->roots[q][v] = w;
       uint32_t x = 1, y = 1;
-      for (int j = 0; j < N / 2; ++j) {
+      for (int j = 0; j < N; ++j) {
         twf[(size_t)q * pl->tw_len + pl->tw_off[v] + j] = h_mont(x, p);
         twi[(size_t)q * pl->tw_len + pl->tw_off[v] + j] = h_mont(y, p);
         x = h_mulmod(x, w, p);
