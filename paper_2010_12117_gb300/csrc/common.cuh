@@ -1,80 +1,15 @@
 // Internal definitions shared by the libpolydet translation units: the plan
-// structure and 32-bit modular arithmetic for primes 2^30 < p < 2^31.
-//
-// Residues live in [0, p).  Multiplication is Montgomery's REDC with
-// R = 2^32 in its signed form: for x < p * 2^32, m = x_lo * p^-1 mod 2^32
-// makes x - m p divisible by 2^32 with the low words cancelling exactly, so
-// x / R mod p = x_hi - umulhi(m, p), a value in (-p, p) that one unsigned
-// min() folds into [0, p).  Because 2p < 2^32, a sum of two products of
-// residues stays below p * 2^32 and needs a single REDC (the fused
-// a*b - c*d of the elimination update).
+// structure, host-side arithmetic, and the launchers of the separate
+// translation units.  Device arithmetic is in modarith.cuh, the per-order
+// launch table of the condensation kernels in teams.cuh.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "../../include/polydet.h"
-
-#define PD_HD __host__ __device__ __forceinline__
-#define PD_D __device__ __forceinline__
-
-struct ModP {
-  uint32_t p;     // the prime
-  uint32_t pinv;  // p^-1 mod 2^32
-  uint32_t r1;    // R mod p      (Montgomery form of 1)
-  uint32_t r2;    // R^2 mod p    (to enter Montgomery form)
-};
-
-PD_D uint32_t redc(uint64_t x, uint32_t p, uint32_t pinv) {
-  uint32_t lo = (uint32_t)x;
-  uint32_t hi = (uint32_t)(x >> 32);
-  uint32_t m = lo * pinv;
-  uint32_t r = hi - __umulhi(m, p);
-  return min(r, r + p);
-}
-
-// a * b / R mod p, valid for a * b < p * 2^32 (e.g. a < 2^32, b < p).
-PD_D uint32_t mmul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
-  return redc((uint64_t)a * b, p, pinv);
-}
-
-// (a*b - c*d) / R mod p for a, b, c, d in [0, p).
-PD_D uint32_t mfms(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t p,
-                   uint32_t pinv) {
-  return redc((uint64_t)a * b + (uint64_t)c * (p - d), p, pinv);
-}
-
-PD_D uint32_t addm(uint32_t a, uint32_t b, uint32_t p) {
-  uint32_t s = a + b;
-  return min(s, s - p);
-}
-
-PD_D uint32_t subm(uint32_t a, uint32_t b, uint32_t p) {
-  uint32_t d = a - b;
-  return min(d, d + p);
-}
-
-// Montgomery-form power: returns (x/R)^e in Montgomery form, x in Montgomery
-// form; `one` is R mod p.
-PD_D uint32_t mpow(uint32_t x, uint32_t e, uint32_t one, uint32_t p, uint32_t pinv) {
-  uint32_t r = one;
-  while (e) {
-    if (e & 1u) r = mmul(r, x, p, pinv);
-    x = mmul(x, x, p, pinv);
-    e >>= 1;
-  }
-  return r;
-}
-
-// Reduce a signed 32-bit coefficient into [0, p) (p > 2^30 so at most two
-// corrections each way).
-PD_D uint32_t reduce_i32(int32_t c, uint32_t p) {
-  int64_t t = c;
-  if (t < 0) t += p;
-  if (t < 0) t += p;
-  if (t >= (int64_t)p) t -= p;
-  return (uint32_t)t;
-}
+#include "modarith.cuh"
+#include "teams.cuh"
 
 // ---------------------------------------------------------------------------
 // Host-side arithmetic used while building plans.
@@ -123,6 +58,11 @@ struct polydet_plan_s {
   uint32_t *d_ninv;       // [P][nvars]   N_v^-1 * R
   uint32_t *d_rn;         // [P]          R^n mod p (condensation output scale)
   uint32_t *d_garner;     // [P][P]       (prod_{l<j} p_l mod p_i) * R, j < i; diagonal: c_i * R
+  // host copies for the CRT kernels of P <= 32 (passed as kernel parameters):
+  // crt_gs[i][j] = -(prod_{l<j} p_l) c_i * R mod p_i (j < i), crt_gs[i][i] = c_i * R,
+  // so that alpha_i = x_i c_i - sum_{j<i} alpha_j (prod_{l<j} p_l) c_i is one dot product
+  uint32_t crt_gs[32 * 32];
+  uint32_t crt_mh[32], crt_mf[32];  // (M - 1) / 2 and M, limbs
   uint32_t *d_mhalf;      // [W] (M-1)/2
   uint32_t *d_mfull;      // [W] M
   uint32_t *d_status;     // 1 word
@@ -211,12 +151,4 @@ PD_HD int node_radix(int d) {
   return lin <= 1 ? 1 : lin <= 2 ? 2 : lin <= 4 ? 4 : 8;
 }
 
-// Lanes per matrix (T) and the resident CTAs of 128 threads the condensation
-// kernel of each order n is compiled for (its __launch_bounds__ minimum),
-// chosen per order from a sweep of both on GB300 with random 31-bit matrices
-// (2^18 nodes): one lane while the whole matrix fits in registers, then the
-// pair that kept the elimination the least latency-bound.
-constexpr int kTeam[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4,
-                                          2, 2, 4, 4, 4, 4, 4, 8, 8, 8, 4, 4, 8, 8, 8, 16};
-constexpr int kMinBlocks[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
-                                               3, 1, 4, 3, 3, 3, 3, 4, 3, 3, 1, 1, 3, 3, 3, 4};
+

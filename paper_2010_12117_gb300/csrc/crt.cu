@@ -72,44 +72,24 @@ __global__ void __launch_bounds__(128) crt_kernel(const uint32_t *__restrict__ r
 }
 
 // The same computation with the prime count a compile-time constant (P <= 32,
-// so W <= P): digits, limbs and the Horner carries stay in registers, the
-// Garner table and the constants sit in shared memory, and a grid-stride
-// loop covers the coefficients.
+// so W <= P): digits, limbs and the Horner carries stay in registers, and a
+// grid-stride loop covers the coefficients.  The constants of the P-prime CRT
+// are passed by value: kernel parameters live in the constant bank, so every
+// table entry (indexed at compile time) is an instruction operand, not a load.
+template <int PT>
+struct CrtTab {
+  uint32_t gs[PT * PT];  // see polydet_plan_s::crt_gs
+  uint32_t p[PT], pinv[PT];
+  uint32_t mh[PT], mf[PT];  // (M - 1) / 2 and M, limbs (zero above W)
+};
+
 template <int PT>
 __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__ res,
                                                     uint32_t *__restrict__ limbs, int64_t C, int W,
-                                                    const ModP *__restrict__ mod,
-                                                    const uint32_t *__restrict__ garner,
-                                                    const uint32_t *__restrict__ mhalf,
-                                                    const uint32_t *__restrict__ mfull) {
-  __shared__ uint32_t gs[PT * PT];
-  __shared__ uint32_t ps[PT], pis[PT], mh[PT], mf[PT];
+                                                    const CrtTab<PT> tab) {
   // per warp: its 32 coefficients' limbs, written out as one contiguous run
   // (coefficients c .. c + 31 own words [c W, (c + 32) W) of the output)
   __shared__ uint32_t stage[256 / 32][32 * PT];
-  // gs[i][j] (j < i) = -G_ij G_ii and gs[i][i] = G_ii (Montgomery forms), so
-  // that alpha_i = x_i G_ii + sum_{j<i} alpha_j (-G_ij G_ii) is one dot
-  // product mod p_i (the Garner step of Sec. 3.4 with its subtraction and
-  // final scaling folded into the constants)
-  for (int f = threadIdx.x; f < PT * PT; f += blockDim.x) {
-    const int i = f / PT, j = f - i * PT;
-    const ModP md = mod[i];
-    uint32_t v = 0u;
-    if (j == i) {
-      v = garner[f];
-    } else if (j < i) {
-      const uint32_t t = mmul(garner[f], garner[i * PT + i], md.p, md.pinv);
-      v = t ? md.p - t : 0u;
-    }
-    gs[f] = v;
-  }
-  for (int i = threadIdx.x; i < PT; i += blockDim.x) {
-    ps[i] = mod[i].p;
-    pis[i] = mod[i].pinv;
-    mh[i] = i < W ? mhalf[i] : 0u;
-    mf[i] = i < W ? mfull[i] : 0u;
-  }
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *sw = stage[warp];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -130,21 +110,23 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
 #pragma unroll
       for (int i = 0; i < PT; ++i) xn[i] = __ldg(res + (int64_t)i * C + c);
     }
+    // Garner digits (Sec. 3.4): alpha_i = x_i c_i - sum_{j<i} alpha_j m_j c_i
+    // mod p_i as one dot product; two 62-bit products (each below 2^31 p_i)
+    // share one REDC
     al[0] = x[0];
 #pragma unroll
     for (int i = 1; i < PT; ++i) {
-      const uint32_t p = ps[i], pinv = pis[i];
-      // terms j <= i: (alpha_j or x_i) * gs[i][j]; two 62-bit products
-      // (each below 2^31 p_i) share one REDC
+      const uint32_t p = tab.p[i], pinv = tab.pinv[i];
       uint32_t acc = 0u;
 #pragma unroll
       for (int j = 0; j <= i; j += 2) {
-        uint64_t sum = (uint64_t)(j < i ? al[j] : x[i]) * gs[i * PT + j];
-        if (j + 1 <= i) sum += (uint64_t)(j + 1 < i ? al[j + 1] : x[i]) * gs[i * PT + j + 1];
+        uint64_t sum = (uint64_t)(j < i ? al[j] : x[i]) * tab.gs[i * PT + j];
+        if (j + 1 <= i) sum += (uint64_t)(j + 1 < i ? al[j + 1] : x[i]) * tab.gs[i * PT + j + 1];
         acc = (j == 0) ? redc(sum, p, pinv) : addm(acc, redc(sum, p, pinv), p);
       }
       al[i] = acc;
     }
+    // mixed radix to binary by Horner: X = (..(alpha_{P-1} p_{P-2} + alpha_{P-2}) ..) p_0 + alpha_0
     uint32_t X[PT];
 #pragma unroll
     for (int w = 0; w < PT; ++w) X[w] = 0u;
@@ -152,7 +134,7 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
 #pragma unroll
     for (int i = PT - 2; i >= 0; --i) {
       uint64_t carry = al[i];
-      const uint32_t pi = ps[i];
+      const uint32_t pi = tab.p[i];
 #pragma unroll
       for (int w = 0; w < PT - i; ++w) {
         const uint64_t t = (uint64_t)X[w] * pi + carry;
@@ -160,15 +142,16 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
         carry = t >> 32;
       }
     }
+    // symmetric lift: X > (M - 1) / 2 becomes X - M (two's complement)
     int cmp = 0;
 #pragma unroll
     for (int w = PT - 1; w >= 0; --w)
-      if (cmp == 0 && w < W) cmp = (X[w] > mh[w]) ? 1 : ((X[w] < mh[w]) ? -1 : 0);
+      if (cmp == 0 && w < W) cmp = (X[w] > tab.mh[w]) ? 1 : ((X[w] < tab.mh[w]) ? -1 : 0);
     if (cmp > 0) {
       uint32_t borrow = 0u;
 #pragma unroll
       for (int w = 0; w < PT; ++w) {
-        const uint64_t t = (uint64_t)X[w] - mf[w] - borrow;
+        const uint64_t t = (uint64_t)X[w] - tab.mf[w] - borrow;
         X[w] = (uint32_t)t;
         borrow = (uint32_t)(t >> 63);
       }
@@ -191,11 +174,18 @@ static int launch_crt_p(const polydet_plan_s *pl, const uint32_t *residues, uint
     int dev = 0, sms = 0;
     PD_CUDA(cudaGetDevice(&dev));
     PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CrtTab<PT> tab;
+    for (int i = 0; i < PT * PT; ++i) tab.gs[i] = pl->crt_gs[i];
+    for (int i = 0; i < PT; ++i) {
+      tab.p[i] = pl->mod_h[i].p;
+      tab.pinv[i] = pl->mod_h[i].pinv;
+      tab.mh[i] = i < pl->W ? pl->crt_mh[i] : 0u;
+      tab.mf[i] = i < pl->W ? pl->crt_mf[i] : 0u;
+    }
     const int threads = 256;
     const int64_t want = (pl->C + threads - 1) / threads;
     const unsigned blocks = (unsigned)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
-    crt_kernel_p<PT><<<blocks, threads, 0, st>>>(residues, limbs, pl->C, pl->W, pl->d_mod,
-                                                 pl->d_garner, pl->d_mhalf, pl->d_mfull);
+    crt_kernel_p<PT><<<blocks, threads, 0, st>>>(residues, limbs, pl->C, pl->W, tab);
     PD_CUDA(cudaGetLastError());
     return POLYDET_OK;
   }

@@ -1,0 +1,75 @@
+// 32-bit modular arithmetic on the device for primes 2^30 < p < 2^31.
+//
+// Residues live in [0, p).  Multiplication is Montgomery's REDC with
+// R = 2^32 in its signed form: for x < p * 2^32, m = x_lo * p^-1 mod 2^32
+// makes x - m p divisible by 2^32 with the low words cancelling exactly, so
+// x / R mod p = x_hi - umulhi(m, p), a value in (-p, p) that one unsigned
+// min() folds into [0, p).  Because 2p < 2^32, a sum of two products of
+// residues stays below p * 2^32 and needs a single REDC (the fused
+// a*b - c*d of the elimination update).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PD_HD __host__ __device__ __forceinline__
+#define PD_D __device__ __forceinline__
+
+struct ModP {
+  uint32_t p;     // the prime
+  uint32_t pinv;  // p^-1 mod 2^32
+  uint32_t r1;    // R mod p      (Montgomery form of 1)
+  uint32_t r2;    // R^2 mod p    (to enter Montgomery form)
+};
+
+PD_D uint32_t redc(uint64_t x, uint32_t p, uint32_t pinv) {
+  uint32_t lo = (uint32_t)x;
+  uint32_t hi = (uint32_t)(x >> 32);
+  uint32_t m = lo * pinv;
+  uint32_t r = hi - __umulhi(m, p);
+  return min(r, r + p);
+}
+
+// a * b / R mod p, valid for a * b < p * 2^32 (e.g. a < 2^32, b < p).
+PD_D uint32_t mmul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
+  return redc((uint64_t)a * b, p, pinv);
+}
+
+// (a*b - c*d) / R mod p for a, b, c, d in [0, p).
+PD_D uint32_t mfms(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t p,
+                   uint32_t pinv) {
+  return redc((uint64_t)a * b + (uint64_t)c * (p - d), p, pinv);
+}
+
+PD_D uint32_t addm(uint32_t a, uint32_t b, uint32_t p) {
+  uint32_t s = a + b;
+  return min(s, s - p);
+}
+
+PD_D uint32_t subm(uint32_t a, uint32_t b, uint32_t p) {
+  uint32_t d = a - b;
+  return min(d, d + p);
+}
+
+// Montgomery-form power: returns (x/R)^e in Montgomery form, x in Montgomery
+// form; `one` is R mod p.
+PD_D uint32_t mpow(uint32_t x, uint32_t e, uint32_t one, uint32_t p, uint32_t pinv) {
+  uint32_t r = one;
+  while (e) {
+    if (e & 1u) r = mmul(r, x, p, pinv);
+    x = mmul(x, x, p, pinv);
+    e >>= 1;
+  }
+  return r;
+}
+
+// Reduce a signed 32-bit coefficient into [0, p) (p > 2^30 so at most two
+// corrections each way).
+PD_D uint32_t reduce_i32(int32_t c, uint32_t p) {
+  int64_t t = c;
+  if (t < 0) t += p;
+  if (t < 0) t += p;
+  if (t >= (int64_t)p) t -= p;
+  return (uint32_t)t;
+}
+

@@ -256,6 +256,21 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
     }
     garner[(size_t)i * nprimes + i] = h_mont(h_powmod(m, p - 2, p), p);
   }
+  if (nprimes <= 32) {
+    for (int i = 0; i < nprimes; ++i) {
+      const uint32_t p = table[i];
+      uint32_t m = 1;
+      for (int j = 0; j < i; ++j) m = h_mulmod(m, table[j] % p, p);
+      const uint32_t ci = h_powmod(m, p - 2, p);  // (prod_{l<i} p_l)^-1 mod p_i
+      uint32_t mj = 1;
+      for (int j = 0; j < i; ++j) {
+        const uint32_t t = h_mulmod(mj, ci, p);
+        pl->crt_gs[i * nprimes + j] = h_mont(t ? p - t : 0u, p);
+        mj = h_mulmod(mj, table[j] % p, p);
+      }
+      pl->crt_gs[i * nprimes + i] = h_mont(ci, p);
+    }
+  }
   // M = prod p as 32-bit limbs; W = ceil(bitlen(M) / 32).
   std::vector<uint32_t> M(nprimes + 1, 0);
   M[0] = 1;
@@ -276,6 +291,10 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
     uint32_t lo = (w == 0) ? (M[0] - 1u) : M[w];
     uint32_t hi_bit = (w + 1 < used) ? (M[w + 1] & 1u) : 0u;
     H[w] = (lo >> 1) | (hi_bit << 31);
+  }
+  for (int w = 0; w < used && w < 32; ++w) {
+    pl->crt_mh[w] = H[w];
+    pl->crt_mf[w] = M[w];
   }
 
   // Caller scratch per prime (words): evaluation keeps its odd passes there,
