@@ -150,7 +150,10 @@ int polydet_condense_batch(polydet_plan_t plan, const uint32_t *evals_dev,
 /* Stage 3, interpolation (Sec. 3.3): on the full grid the inverse NTT with the
  * 1/N factor, keeping the C coefficients with e_v <= D_v (any nonzero
  * coefficient with e_v > D_v sets POLYDET_STATUS_BOUND); on the node grid the
- * inverse Vandermonde matrix of the nodes, one variable at a time.  detvals_dev: device uint32
+ * unique interpolant through the nodes, one variable at a time, solved coset
+ * by coset (an inverse DFT of size L per whole coset, then L inverse
+ * Vandermonde solves of size M_v / L and a correction from the last partial
+ * coset).  detvals_dev: device uint32
  * [prime_hi - prime_lo][G] (read only); residues_dev: device uint32
  * [prime_hi - prime_lo][C]; ws_dev: device scratch of
  * (prime_hi - prime_lo) * info.interp_ws_words words (NULL allowed when 0).

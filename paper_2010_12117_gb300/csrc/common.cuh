@@ -42,9 +42,9 @@ struct polydet_plan_s {
   int M[POLYDET_MAX_VARS];
   int LPo[POLYDET_MAX_VARS];  // node order: node k is w^(k / LPo + (N / LPo)(k mod LPo))
   int full;                        // 1: full power-of-two grid + inverse NTT
-  int vinv_off[POLYDET_MAX_VARS];  // node grid: offset of variable v's table
-  int vinv_len;                    // node grid: sum_v M_v^2 words per prime
-  uint32_t *d_vinv;                // [P][vinv_len] inverse Vandermonde * R
+  int itab_off[POLYDET_MAX_VARS];  // node grid: offset of variable v's interpolation tables
+  int itab_len;                    // node grid: their words per prime
+  uint32_t *d_itab;                // [P][itab_len] (layout in plan.cu, Montgomery forms)
   int tw_len;                      // sum_v N_v: twiddles per prime
   uint32_t primes[POLYDET_MAX_PRIMES];
   uint32_t roots[POLYDET_MAX_PRIMES][POLYDET_MAX_VARS];

@@ -407,35 +407,87 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
   return POLYDET_OK;
 }
 
-// Node-grid interpolation of one variable: every column (a, b) of the tensor
-// [A][m][B] holds the values at the nodes w^0..w^(m-1) of a polynomial of
-// degree < m in that variable; its coefficients are V^-1 y (V the Vandermonde
-// matrix of the nodes, its inverse in Montgomery form in `vinv`).  A CTA
-// stages Ct columns x m values in shared memory; each thread then forms
-// output coefficients as dot products with rows of V^-1, read by every lane
-// of a warp at the same address (broadcast).
-struct VmArgs {
+// Node-grid interpolation of one variable (Sec. 3.3 on the node grid): every
+// column (a, b) of the tensor [A][m][B] holds the values at the m nodes (in
+// coset order: node k = j L + t is w^j psi^t, psi = w^(N/L)) of a polynomial
+// P of degree < m in that variable; its coefficients replace them.  With
+// P(x) = sum_{r<L} x^r Q_r(x^L) and x^L = z_j = w^(L j) on coset j:
+//  1. per whole coset j < Jf: an inverse DFT of size L of its L values, times
+//     L^-1 w^(-j r), gives Q_r(z_j) for every r;
+//  2. per r: the Jf coefficients through z_0..z_{Jf-1} (inverse Vandermonde
+//     of size Jf: Jf^2 L products instead of m^2);
+//  3. the s = m - Jf L nodes of the last coset fix the top coefficient
+//     lambda_r of Q_r for r < s (Q_r = interpolant + lambda_r Pi, Pi =
+//     prod_j (z - z_j)): an s x s solve after subtracting the known part.
+// A CTA stages Ct columns; every phase runs over (row, column) items.
+struct CiArgs {
   const uint32_t *in;
   uint32_t *out;
   int64_t in_prime_stride, out_prime_stride;
   int64_t A, B;
-  int m, Ct;
+  int m, Jf, s, Ct;
   int prime_lo;
   const ModP *mod;
-  const uint32_t *vinv;  // this variable's table for prime 0
-  int vinv_len;          // words per prime
+  const uint32_t *tab;  // this variable's tables for prime 0
+  int tab_len;          // words per prime
 };
 
-__global__ void __launch_bounds__(256) vmat_kernel(VmArgs a) {
+// Sum of two products of residues reduced once (2 p^2 < p 2^32).
+PD_D uint32_t mac2(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, uint32_t p, uint32_t pinv) {
+  return redc((uint64_t)a0 * b0 + (uint64_t)a1 * b1, p, pinv);
+}
+
+// X_r = sum_t x_t rho^(t r) for L in {1, 2, 4, 8}; rk[k] = rho^k (Montgomery).
+template <int L>
+PD_D void small_dft(uint32_t (&x)[L], const uint32_t *rk, uint32_t p, uint32_t pinv) {
+  if constexpr (L == 2) {
+    const uint32_t a = x[0], b = x[1];
+    x[0] = addm(a, b, p);
+    x[1] = subm(a, b, p);
+  } else if constexpr (L == 4) {
+    uint32_t y[4], xx[4] = {x[0], x[1], x[2], x[3]};
+    dft4<false, false, false, false>(xx, y, __ldg(rk + 1), p, pinv);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) x[r] = y[r];
+  } else if constexpr (L == 8) {
+    uint32_t xe[4] = {x[0], x[2], x[4], x[6]}, xo[4] = {x[1], x[3], x[5], x[7]}, E[4], O[4];
+    const uint32_t r2 = __ldg(rk + 2);
+    dft4<false, false, false, false>(xe, E, r2, p, pinv);
+    dft4<false, false, false, false>(xo, O, r2, p, pinv);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t o = r ? mmul(__ldg(rk + r), O[r], p, pinv) : O[r];
+      x[r] = addm(E[r], o, p);
+      x[r + 4] = subm(E[r], o, p);
+    }
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) cinterp_kernel(CiArgs a) {
   extern __shared__ uint32_t sm[];
   const int q = a.prime_lo + blockIdx.z;
   const ModP md = a.mod[q];
-  const int m = a.m, Ct = a.Ct, S = Ct + 1;
+  const uint32_t p = md.p, pinv = md.pinv;
+  const int m = a.m, Jf = a.Jf, s = a.s, Ct = a.Ct, S = Ct + 1;
   const int64_t ncols = a.A * a.B;
   const int64_t col0 = (int64_t)blockIdx.x * Ct;
   const uint32_t *in = a.in + (int64_t)blockIdx.z * a.in_prime_stride;
   uint32_t *out = a.out + (int64_t)blockIdx.z * a.out_prime_stride;
-  for (int f = threadIdx.x; f < m * Ct; f += blockDim.x) {
+  const uint32_t *tab = a.tab + (size_t)q * a.tab_len;
+  const uint32_t *VfInv = tab;
+  const uint32_t *tw1 = VfInv + Jf * Jf;
+  const uint32_t *rk = tw1 + Jf * L;
+  const uint32_t *H = rk + L;
+  const uint32_t *Bm = H + s * L * Jf;
+  const uint32_t *pic = Bm + s * s;
+  uint32_t *Y = sm;                      // [m][S]   node values
+  uint32_t *Qv = Y + (size_t)m * S;      // [L][Jf][S] Q_r(z_j)
+  uint32_t *Qt = Qv + (size_t)L * Jf * S;  // [L][Jf + 1][S] coefficients of Q_r
+  uint32_t *Dv = Qt + (size_t)L * (Jf + 1) * S;  // [s][L][S] partial sums, then [s][S] residuals
+  const int tid = threadIdx.x, bd = blockDim.x;
+
+  for (int f = tid; f < m * Ct; f += bd) {
     const int r = f / Ct, c = f - r * Ct;
     const int64_t col = col0 + c;
     uint32_t v = 0u;
@@ -443,50 +495,121 @@ __global__ void __launch_bounds__(256) vmat_kernel(VmArgs a) {
       const int64_t aa = col / a.B, bb = col - aa * a.B;
       v = in[(aa * m + r) * a.B + bb];
     }
-    sm[r * S + c] = v;
+    Y[r * S + c] = v;
   }
   __syncthreads();
-  const uint32_t *V = a.vinv + (size_t)q * a.vinv_len;
-  for (int f = threadIdx.x; f < m * Ct; f += blockDim.x) {
+  // 1. inverse DFT of each whole coset, twisted: Qv[r][j] = Q_r(z_j)
+  for (int f = tid; f < Jf * Ct; f += bd) {
+    const int j = f / Ct, c = f - j * Ct;
+    uint32_t x[L];
+#pragma unroll
+    for (int t = 0; t < L; ++t) x[t] = Y[(j * L + t) * S + c];
+    small_dft<L>(x, rk, p, pinv);
+#pragma unroll
+    for (int r = 0; r < L; ++r) Qv[(r * Jf + j) * S + c] = mmul(x[r], __ldg(tw1 + j * L + r), p, pinv);
+  }
+  __syncthreads();
+  // 2. Qt[r][u] = sum_j VfInv[u][j] Qv[r][j]; Qt[r][Jf] = 0
+  for (int f = tid; f < L * (Jf + 1) * Ct; f += bd) {
+    const int ru = f / Ct, c = f - ru * Ct;
+    const int r = ru / (Jf + 1), u = ru - r * (Jf + 1);
+    uint32_t acc = 0u;
+    if (u < Jf) {
+      const uint32_t *row = VfInv + u * Jf;
+      const uint32_t *qv = Qv + (size_t)r * Jf * S + c;
+      int j = 0;
+      for (; j + 1 < Jf; j += 2)
+        acc = addm(acc, mac2(__ldg(row + j), qv[j * S], __ldg(row + j + 1), qv[(j + 1) * S], p, pinv), p);
+      if (j < Jf) acc = addm(acc, mmul(__ldg(row + j), qv[j * S], p, pinv), p);
+    }
+    Qt[ru * S + c] = acc;
+  }
+  __syncthreads();
+  if (s > 0) {
+    // 3a. partial sums of the known part at the last coset's nodes
+    for (int f = tid; f < s * L * Ct; f += bd) {
+      const int tr = f / Ct, c = f - tr * Ct;
+      const int r = tr % L;
+      const uint32_t *h = H + tr * Jf;
+      const uint32_t *qt = Qt + (size_t)r * (Jf + 1) * S + c;
+      uint32_t acc = 0u;
+      int u = 0;
+      for (; u + 1 < Jf; u += 2)
+        acc = addm(acc, mac2(__ldg(h + u), qt[u * S], __ldg(h + u + 1), qt[(u + 1) * S], p, pinv), p);
+      if (u < Jf) acc = addm(acc, mmul(__ldg(h + u), qt[u * S], p, pinv), p);
+      Dv[tr * S + c] = acc;
+    }
+    __syncthreads();
+    // 3b. residuals d_t = y_{Jf L + t} - sum_r partial[t][r] (into row t L)
+    for (int f = tid; f < s * Ct; f += bd) {
+      const int t = f / Ct, c = f - t * Ct;
+      uint32_t k = 0u;
+      for (int r = 0; r < L; ++r) k = addm(k, Dv[(t * L + r) * S + c], p);
+      Dv[(t * L) * S + c] = subm(Y[(Jf * L + t) * S + c], k, p);
+    }
+    __syncthreads();
+    // 3c. lambda_r = sum_t B[r][t] d_t, then Qt[r][u] += lambda_r pi_u (r < s)
+    for (int f = tid; f < s * Ct; f += bd) {
+      const int r = f / Ct, c = f - r * Ct;
+      uint32_t lam = 0u;
+      for (int t = 0; t < s; ++t) lam = addm(lam, mmul(__ldg(Bm + r * s + t), Dv[(t * L) * S + c], p, pinv), p);
+      Y[r * S + c] = lam;  // the node values are no longer needed (rows < s <= m)
+    }
+    __syncthreads();
+    for (int f = tid; f < s * (Jf + 1) * Ct; f += bd) {
+      const int ru = f / Ct, c = f - ru * Ct;
+      const int r = ru / (Jf + 1), u = ru - r * (Jf + 1);
+      Qt[ru * S + c] = addm(Qt[ru * S + c], mmul(Y[r * S + c], __ldg(pic + u), p, pinv), p);
+    }
+    __syncthreads();
+  }
+  // 4. coefficient e = L u + r of each column is Qt[r][u]
+  for (int f = tid; f < m * Ct; f += bd) {
     const int e = f / Ct, c = f - e * Ct;
     const int64_t col = col0 + c;
     if (col >= ncols) continue;
-    const uint32_t *row = V + (size_t)e * m;
-    uint32_t acc = 0u;
-    int i = 0;
-    for (; i + 1 < m; i += 2) {  // two products per REDC: 2 p^2 < p 2^32
-      const uint64_t s2 = (uint64_t)__ldg(row + i) * sm[i * S + c] +
-                          (uint64_t)__ldg(row + i + 1) * sm[(i + 1) * S + c];
-      acc = addm(acc, redc(s2, md.p, md.pinv), md.p);
-    }
-    if (i < m) acc = addm(acc, mmul(__ldg(row + i), sm[i * S + c], md.p, md.pinv), md.p);
+    const int r = e % L, u = e / L;
     const int64_t aa = col / a.B, bb = col - aa * a.B;
-    out[(aa * m + e) * a.B + bb] = acc;
+    out[(aa * m + e) * a.B + bb] = Qt[(r * (Jf + 1) + u) * S + c];
   }
+}
+
+static size_t cinterp_rows(int m, int L) {
+  const int Jf = m / L, s = m % L;
+  return (size_t)m + (size_t)L * Jf + (size_t)L * (Jf + 1) + (size_t)s * L;
 }
 
 static int interp_nodes(polydet_plan_t pl, const uint32_t *detvals, int lo, int hi,
                         uint32_t *residues, uint32_t *ws, cudaStream_t st) {
   const int k = pl->nvars, np = hi - lo;
   const uint64_t slot = pl->interp_ws_words / 2;
+  constexpr size_t kMaxSmem = 200 * 1024;
   static bool attr_set = false;
   if (!attr_set) {
-    PD_CUDA(cudaFuncSetAttribute(vmat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    PD_CUDA(cudaFuncSetAttribute(cinterp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PD_CUDA(cudaFuncSetAttribute(cinterp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PD_CUDA(cudaFuncSetAttribute(cinterp_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PD_CUDA(cudaFuncSetAttribute(cinterp_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     attr_set = true;
   }
   const uint32_t *cur = detvals;
   int64_t cur_prime = pl->G;
   int t = 0;
   for (int v = k - 1; v >= 0; --v, ++t) {
-    VmArgs a = {};
+    CiArgs a = {};
     a.A = 1;
     for (int u = 0; u < v; ++u) a.A *= pl->M[u];
     a.B = 1;
     for (int u = v + 1; u < k; ++u) a.B *= pl->M[u];
+    const int L = pl->LPo[v];
     a.m = pl->M[v];
+    a.Jf = a.m / L;
+    a.s = a.m % L;
+    const size_t rows = cinterp_rows(a.m, L);
     int ct = 32;
-    while (ct > 1 && (int64_t)a.m * (ct + 1) > 16384) ct >>= 1;
+    while (ct > 1 && rows * (ct + 1) * sizeof(uint32_t) > 48 * 1024) ct >>= 1;
     while (ct > 1 && ct / 2 >= a.A * a.B) ct >>= 1;
+    if (rows * (ct + 1) * sizeof(uint32_t) > kMaxSmem) return POLYDET_EINVAL;
     a.Ct = ct;
     a.in = cur;
     a.in_prime_stride = cur_prime;
@@ -499,11 +622,16 @@ static int interp_nodes(polydet_plan_t pl, const uint32_t *detvals, int lo, int 
     }
     a.prime_lo = lo;
     a.mod = pl->d_mod;
-    a.vinv = pl->d_vinv + pl->vinv_off[v];
-    a.vinv_len = pl->vinv_len;
-    const size_t smem = (size_t)a.m * (ct + 1) * sizeof(uint32_t);
+    a.tab = pl->d_itab + pl->itab_off[v];
+    a.tab_len = pl->itab_len;
+    const size_t smem = rows * (ct + 1) * sizeof(uint32_t);
     dim3 grid((unsigned)((a.A * a.B + ct - 1) / ct), 1, (unsigned)np);
-    vmat_kernel<<<grid, 256, smem, st>>>(a);
+    switch (L) {
+      case 1: cinterp_kernel<1><<<grid, 256, smem, st>>>(a); break;
+      case 2: cinterp_kernel<2><<<grid, 256, smem, st>>>(a); break;
+      case 4: cinterp_kernel<4><<<grid, 256, smem, st>>>(a); break;
+      default: cinterp_kernel<8><<<grid, 256, smem, st>>>(a); break;
+    }
     PD_CUDA(cudaGetLastError());
     cur = a.out;
     cur_prime = a.out_prime_stride;

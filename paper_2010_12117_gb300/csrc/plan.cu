@@ -132,6 +132,110 @@ static int pow2_at_least(int64_t x) {
   return (int)n;
 }
 
+// Words of the interpolation tables of one variable (see polydet_plan).
+static int itab_words(int M, int L) {
+  const int Jf = M / L, s = M % L;
+  return Jf * Jf + Jf * L + L + s * L * Jf + s * s + Jf + 1;
+}
+
+// Inverse of an n x n matrix mod p by Gauss-Jordan (n < 8 here; always
+// invertible: a scaled Vandermonde matrix of distinct nodes).
+static std::vector<uint64_t> mat_inv_mod(std::vector<uint64_t> A, int n, uint64_t p) {
+  std::vector<uint64_t> I((size_t)n * n, 0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1;
+  for (int c = 0; c < n; ++c) {
+    int r = c;
+    while (r < n && A[(size_t)r * n + c] == 0) ++r;
+    for (int k = 0; k < n; ++k) {
+      std::swap(A[(size_t)c * n + k], A[(size_t)r * n + k]);
+      std::swap(I[(size_t)c * n + k], I[(size_t)r * n + k]);
+    }
+    const uint64_t iv = h_powmod((uint32_t)A[(size_t)c * n + c], p - 2, (uint32_t)p);
+    for (int k = 0; k < n; ++k) {
+      A[(size_t)c * n + k] = A[(size_t)c * n + k] * iv % p;
+      I[(size_t)c * n + k] = I[(size_t)c * n + k] * iv % p;
+    }
+    for (int i = 0; i < n; ++i) {
+      if (i == c || A[(size_t)i * n + c] == 0) continue;
+      const uint64_t f = A[(size_t)i * n + c];
+      for (int k = 0; k < n; ++k) {
+        A[(size_t)i * n + k] = (A[(size_t)i * n + k] + (p - f) * A[(size_t)c * n + k]) % p;
+        I[(size_t)i * n + k] = (I[(size_t)i * n + k] + (p - f) * I[(size_t)c * n + k]) % p;
+      }
+    }
+  }
+  return I;
+}
+
+// The interpolation tables of one (prime, variable), in the layout of
+// polydet_plan's comment.  They depend on (p, w, N, L, M) only and are
+// memoised for the process.
+static void interp_tables(uint32_t p32, uint32_t w32, int N, int L, int M, uint32_t *dst) {
+  static std::mutex mu;
+  static std::map<std::tuple<uint32_t, uint32_t, int, int>, std::vector<uint32_t>> cache;
+  const auto key = std::make_tuple(p32, w32, L, M);
+  const int words = itab_words(M, L);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      memcpy(dst, it->second.data(), (size_t)words * sizeof(uint32_t));
+      return;
+    }
+  }
+  const uint64_t p = p32, w = w32;
+  auto pw = [&](uint64_t b, uint64_t e) { return (uint64_t)h_powmod((uint32_t)b, e, p32); };
+  auto inv = [&](uint64_t a) { return (uint64_t)h_powmod((uint32_t)(a % p), p - 2, p32); };
+  auto mont = [&](uint64_t a) { return h_mont((uint32_t)(a % p), p32); };
+  const int Jf = M / L, s = M % L;
+  const uint64_t psi = pw(w, (uint64_t)(N / L)), ipsi = inv(psi);
+  std::vector<uint64_t> z(Jf + 1);
+  for (int j = 0; j <= Jf; ++j) z[j] = pw(w, (uint64_t)L * j);
+  uint32_t *o = dst;
+  // VfInv by Lagrange: Vf^-1[u][j] = [z^u] q_j(z) / q_j(z_j), q_j = Pi / (z - z_j)
+  std::vector<uint64_t> pic(Jf + 1, 0);  // Pi(z), built factor by factor
+  pic[0] = 1;
+  for (int j = 0; j < Jf; ++j) {
+    for (int k = j + 1; k >= 1; --k) pic[k] = (pic[k - 1] + (p - z[j]) * pic[k]) % p;
+    pic[0] = (p - z[j]) * pic[0] % p;
+  }
+  std::vector<uint64_t> qc(Jf > 0 ? Jf : 1);
+  for (int j = 0; j < Jf; ++j) {
+    qc[Jf - 1] = 1;  // q_j = Pi / (z - z_j): q_{k-1} = pi_k + z_j q_k
+    for (int k = Jf - 1; k >= 1; --k) qc[k - 1] = (pic[k] + z[j] * qc[k]) % p;
+    uint64_t den = 0;
+    for (int k = Jf - 1; k >= 0; --k) den = (den * z[j] + qc[k]) % p;
+    const uint64_t id = inv(den);
+    for (int u = 0; u < Jf; ++u) o[(size_t)u * Jf + j] = mont(qc[u] * id % p);
+  }
+  o += (size_t)Jf * Jf;
+  const uint64_t Linv = inv((uint64_t)L);
+  for (int j = 0; j < Jf; ++j)
+    for (int r = 0; r < L; ++r) o[(size_t)j * L + r] = mont(Linv * inv(pw(w, (uint64_t)j * r)) % p);
+  o += (size_t)Jf * L;
+  for (int k = 0; k < L; ++k) o[k] = mont(pw(ipsi, (uint64_t)k));
+  o += L;
+  for (int t = 0; t < s; ++t)
+    for (int r = 0; r < L; ++r)
+      for (int u = 0; u < Jf; ++u)
+        o[((size_t)t * L + r) * Jf + u] =
+            mont(pw(psi, (uint64_t)t * r) * pw(w, (uint64_t)Jf * r) % p * pw(z[Jf], (uint64_t)u) % p);
+  o += (size_t)s * L * Jf;
+  if (s > 0) {
+    uint64_t piz = 0;  // Pi(z_Jf)
+    for (int k = Jf; k >= 0; --k) piz = (piz * z[Jf] + pic[k]) % p;
+    std::vector<uint64_t> A((size_t)s * s);
+    for (int t = 0; t < s; ++t)
+      for (int r = 0; r < s; ++r) A[(size_t)t * s + r] = pw(psi, (uint64_t)t * r) * pw(w, (uint64_t)Jf * r) % p * piz % p;
+    const std::vector<uint64_t> B = mat_inv_mod(A, s, p);
+    for (int i = 0; i < s * s; ++i) o[i] = mont(B[i]);
+  }
+  o += (size_t)s * s;
+  for (int k = 0; k <= Jf; ++k) o[k] = mont(pic[k]);
+  std::lock_guard<std::mutex> lock(mu);
+  cache.emplace(key, std::vector<uint32_t>(dst, dst + words));
+}
+
 static void free_plan(polydet_plan_s *pl) {
   if (!pl) return;
   cudaFree(pl->d_mod);
@@ -143,7 +247,7 @@ static void free_plan(polydet_plan_s *pl) {
   cudaFree(pl->d_mhalf);
   cudaFree(pl->d_mfull);
   cudaFree(pl->d_status);
-  cudaFree(pl->d_vinv);
+  cudaFree(pl->d_itab);
   delete pl;
 }
 
@@ -312,58 +416,34 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
     if (s > interp_slot) interp_slot = s;
   }
 
-  // Node grid: inverse of the Vandermonde matrix of the nodes x_i = w^i,
-  // i <= D (Sec. 3.3: the interpolating polynomial of degree <= D through
-  // D + 1 distinct nodes is unique).  With m(x) = prod_j (x - x_j) and
-  // q_i(x) = m(x) / (x - x_i) (synthetic division), the Lagrange basis is
-  // q_i / q_i(x_i), so V^-1[e][i] = [x^e] q_i / q_i(x_i).  O(D^2) per table.
-  std::vector<uint32_t> vinv;
+  // Node grid interpolation tables (Sec. 3.3: the interpolating polynomial of
+  // degree < M through M distinct nodes is unique), for the coset-structured
+  // solve of ntt.cu: with the nodes in coset order (L = LPo[v], Jf = M / L
+  // whole cosets, s = M mod L nodes of one more), P(x) = sum_r x^r Q_r(x^L)
+  // and x^L = z_j = w^(L j) on coset j, so an inverse DFT of size L per coset
+  // gives Q_r(z_j) and each Q_r is interpolated through z_0..z_{Jf-1}; the
+  // last s nodes fix the top coefficient of Q_r for r < s.  Per (prime,
+  // variable), Montgomery forms:
+  //   VfInv [Jf][Jf]   inverse Vandermonde of z_0..z_{Jf-1} (V[j][u] = z_j^u)
+  //   tw1   [Jf][L]    L^-1 w^(-j r)
+  //   ipsi  [L]        psi^-k, psi = w^(N / L)
+  //   H     [s][L][Jf] psi^(t r) w^(Jf r) z_Jf^u
+  //   B     [s][s]     inverse of A[t][r] = psi^(t r) w^(Jf r) Pi(z_Jf), r, t < s
+  //   pi    [Jf + 1]   coefficients of Pi(z) = prod_{j<Jf} (z - z_j)
+  std::vector<uint32_t> itab;
   pl->full = (flags & POLYDET_FLAG_FULL_GRID) ? 1 : 0;
   if (!pl->full) {
     int off2 = 0;
     for (int v = 0; v < nvars; ++v) {
-      pl->vinv_off[v] = off2;
-      off2 += pl->M[v] * pl->M[v];
+      pl->itab_off[v] = off2;
+      off2 += itab_words(pl->M[v], pl->LPo[v]);
     }
-    pl->vinv_len = off2;
-    vinv.assign((size_t)nprimes * off2, 0u);
+    pl->itab_len = off2;
+    itab.assign((size_t)nprimes * off2, 0u);
     for (int q = 0; q < nprimes; ++q) {
-      const uint64_t p = table[q];
       for (int v = 0; v < nvars; ++v) {
-        const int m = pl->M[v];
-        uint32_t *dst0 = vinv.data() + (size_t)q * off2 + pl->vinv_off[v];
-        // tables depend on (p, w, m) only: compute each once per process
-        static std::mutex vmu;
-        static std::map<std::tuple<uint32_t, uint32_t, int, int>, std::vector<uint32_t>> vcache;
-        const auto key = std::make_tuple((uint32_t)p, pl->roots[q][v], m, pl->LPo[v]);
-        {
-          std::lock_guard<std::mutex> lock(vmu);
-          auto it = vcache.find(key);
-          if (it != vcache.end()) {
-            memcpy(dst0, it->second.data(), (size_t)m * m * sizeof(uint32_t));
-            continue;
-          }
-        }
-        std::vector<uint64_t> x(m), mc(m + 1, 0), qc(m);
-        for (int i = 0; i < m; ++i)  // the nodes in the plan's order
-          x[i] = h_powmod(pl->roots[q][v], (uint64_t)node_exp(i, pl->N[v], pl->LPo[v]), (uint32_t)p);
-        mc[0] = 1;  // m(x), built factor by factor; mc[k] = coefficient of x^k
-        for (int j = 0; j < m; ++j) {
-          for (int k = j + 1; k >= 1; --k) mc[k] = (mc[k - 1] + (p - x[j]) * mc[k]) % p;
-          mc[0] = (p - x[j]) * mc[0] % p;
-        }
-        uint32_t *dst = vinv.data() + (size_t)q * off2 + pl->vinv_off[v];
-        for (int i = 0; i < m; ++i) {
-          qc[m - 1] = 1;  // q_i = m / (x - x_i): q_{k-1} = m_k + x_i q_k
-          for (int k = m - 1; k >= 1; --k) qc[k - 1] = (mc[k] + x[i] * qc[k]) % p;
-          uint64_t den = 0;  // q_i(x_i) by Horner
-          for (int k = m - 1; k >= 0; --k) den = (den * x[i] + qc[k]) % p;
-          const uint64_t inv = h_powmod((uint32_t)den, p - 2, (uint32_t)p);
-          for (int e = 0; e < m; ++e)
-            dst[(size_t)e * m + i] = h_mont((uint32_t)(qc[e] * inv % p), (uint32_t)p);
-        }
-        std::lock_guard<std::mutex> lock(vmu);
-        vcache.emplace(key, std::vector<uint32_t>(dst, dst + (size_t)m * m));
+        uint32_t *dst = itab.data() + (size_t)q * off2 + pl->itab_off[v];
+        interp_tables(table[q], pl->roots[q][v], pl->N[v], pl->LPo[v], pl->M[v], dst);
       }
     }
   }
@@ -376,7 +456,7 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
       (rc = upload(&pl->d_rn, rn)) || (rc = upload(&pl->d_garner, garner)) ||
       (rc = upload(&pl->d_mhalf, H)) || (rc = upload(&pl->d_mfull, M)) ||
       (rc = upload(&pl->d_status, std::vector<uint32_t>(1, 0u))) ||
-      (!pl->full && (rc = upload(&pl->d_vinv, vinv)))) {
+      (!pl->full && (rc = upload(&pl->d_itab, itab)))) {
     free_plan(pl);
     return rc;
   }
