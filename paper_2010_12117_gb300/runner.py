@@ -296,8 +296,42 @@ class BatchedRunner:
                 timer.run(name, stream, fn, work)
 
     def download(self, stream: torch.cuda.Stream) -> None:
+        self._last_host = self.host_out
         with torch.cuda.stream(stream):
             self.host_out.copy_(self.limbs, non_blocking=True)
+
+    def run_pipelined(self, steps: int, stream: torch.cuda.Stream,
+                      copy_stream: Optional[torch.cuda.Stream] = None) -> None:
+        """``steps`` full runs end to end - upload of the inputs from pinned
+        host memory, compute, download of the limbs to pinned host memory -
+        with each run's download overlapping the next run's compute: the
+        limbs go to one of two device staging buffers (a device copy) and
+        from there to host on ``copy_stream``.  Returns after everything has
+        landed; results() then reads the last run's limbs."""
+        cs = copy_stream or torch.cuda.Stream()
+        if getattr(self, "_stage", None) is None:
+            self._stage = [torch.empty_like(self.limbs) for _ in range(2)]
+            self._host2 = [self.host_out, torch.empty_like(self.host_out, pin_memory=True)]
+        free = [None, None]  # copy-stream events: staging slot read out
+        for k in range(steps):
+            slot = k % 2
+            self.upload(stream)
+            self.compute(stream)
+            if free[slot] is not None:
+                stream.wait_event(free[slot])
+            with torch.cuda.stream(stream):
+                self._stage[slot].copy_(self.limbs, non_blocking=True)
+            ready = torch.cuda.Event()
+            ready.record(stream)
+            cs.wait_event(ready)
+            with torch.cuda.stream(cs):
+                self._host2[slot].copy_(self._stage[slot], non_blocking=True)
+            free[slot] = torch.cuda.Event()
+            free[slot].record(cs)
+        cs.synchronize()
+        stream.synchronize()
+        if steps:
+            self._last_host = self._host2[(steps - 1) % 2]
 
     def check_status(self, stream: torch.cuda.Stream) -> None:
         st = self.batch.sync_status(stream)
@@ -306,7 +340,7 @@ class BatchedRunner:
 
     def results(self) -> List[List[int]]:
         out = []
-        host = self.host_out.numpy().view(np.uint32)
+        host = getattr(self, "_last_host", self.host_out).numpy().view(np.uint32)
         lo = self.batch.offsets["limbs"]
         for j, info in enumerate(self.batch.job_info):
             C, W = int(info.C), int(info.W)
@@ -318,7 +352,7 @@ class BatchedRunner:
         ordered, no device synchronisation); the batch's small plan tables
         stay until close()."""
         self.graph = None
-        for name in ("coeffs_dev", "partial", "detvals", "residues", "limbs", "ws"):
+        for name in ("coeffs_dev", "partial", "detvals", "residues", "limbs", "ws", "_stage"):
             setattr(self, name, None)
 
     def close(self) -> None:

@@ -164,3 +164,19 @@ def test_last_variable_degree_limit():
     from paper_2010_12117_gb300.binding import Batch, PolydetError
     with pytest.raises(PolydetError):
         Batch([(4, (1, 8), 2)])
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3])
+def test_pipelined_end_to_end_runs_give_the_same_limbs(steps):
+    """Upload, compute and download with each download overlapping the next
+    run's compute: the results equal a plain run's."""
+    from paper_2010_12117_gb300.runner import BatchedRunner
+    mats = _mixed()[:14]
+    want = batched_results(mats)
+    st = torch.cuda.Stream()
+    r = BatchedRunner(mats, tune=False, stream=st)
+    r.capture(st)
+    r.run_pipelined(steps, st)
+    r.check_status(st)
+    assert r.results() == want
+    r.close()
