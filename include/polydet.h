@@ -212,9 +212,12 @@ int polydet_sync_status(polydet_plan_t plan, void *stream, uint32_t *status_out)
  *     persistent kernel per order takes (job, prime, node-block) items from
  *     a counter kept in the caller's workspace;
  *   POLYDET_BATCH_MATERIALIZED: the first variable's NTT pass writes the
- *     evaluated matrices of a chunk of primes into the workspace and the
- *     condensation kernel of polydet_condense_batch reads them back (cheaper
- *     per node than fused evaluation when n^2 entries dominate).
+ *     evaluated matrices of a chunk of primes into one of two workspace
+ *     buffers and the condensation kernel of polydet_condense_batch reads
+ *     them back (cheaper per node than fused evaluation when n^2 entries
+ *     dominate); the passes run on a stream of the batch's own, joined to the
+ *     caller's stream by events, so a pass overlaps the previous chunk's
+ *     condensation and the whole run still captures into one CUDA graph.
  * The default is fused for n < POLYDET_BATCH_MATERIALIZE_N, materialized
  * from there on; polydet_batch_set_mode changes it per order (the
  * autotuner's second knob).

@@ -46,6 +46,12 @@ struct polydet_batch_s {
   int mode[POLYDET_MAX_N + 1] = {};
   std::vector<int> jobs_of[POLYDET_MAX_N + 1];
   uint64_t chunk_words = POLYDET_BATCH_CHUNK_WORDS;
+  uint64_t chunk_max = 0;  // words of the largest materialized chunk (one of two buffers)
+  // materialized chunks: first-variable passes on `side`, condensation on the
+  // caller's stream; ev[0..1] = pass of buffer b done, ev[2..3] = condensation
+  // of buffer b done, ev[4] / ev[5] = fork / join
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev[6] = {};
 };
 
 // Primes of job `pl` per materialized chunk: as many as fit in the chunk
@@ -59,7 +65,7 @@ static int chunk_primes(const polydet_batch_s *b, const polydet_plan_s *pl) {
 // Workspace words for the current modes: the counters, then the largest
 // scratch any job needs in any stage (stages run one after another).
 static void update_ws(polydet_batch_s *b) {
-  uint64_t ws = 0;
+  uint64_t ws = 0, cmax = 0;
   for (int j = 0; j < b->njobs; ++j) {
     const polydet_plan_s *pl = b->plans[j];
     uint64_t need = pl->interp_ws_words * (uint64_t)pl->P;
@@ -67,11 +73,13 @@ static void update_ws(polydet_batch_s *b) {
       if (pl->nvars > 1) need = std::max<uint64_t>(need, pd_partial_ws_words(pl) * (uint64_t)pl->P);
     } else {
       need = std::max<uint64_t>(need, pd_head_ws_words(pl));
-      need = std::max<uint64_t>(need, (uint64_t)chunk_primes(b, pl) * pl->n * pl->n *
+      cmax = std::max<uint64_t>(cmax, (uint64_t)chunk_primes(b, pl) * pl->n * pl->n *
                                           (uint64_t)pd_tail_layout(pl).entry);
     }
     ws = std::max(ws, need);
   }
+  b->chunk_max = (cmax + 63) / 64 * 64;
+  ws = std::max<uint64_t>(ws, 2 * b->chunk_max);  // two chunk buffers, filled alternately
   b->ws_words = kWsHead + ws;
 }
 
@@ -79,6 +87,9 @@ static void destroy_batch(polydet_batch_s *b) {
   if (!b) return;
   for (auto p : b->plans) polydet_plan_destroy(p);
   for (int n = 0; n <= POLYDET_MAX_N; ++n) cudaFree(b->d_segs[n]);
+  for (auto e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->side) cudaStreamDestroy(b->side);
   delete b;
 }
 
@@ -159,6 +170,16 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
   for (int n = 1; n <= POLYDET_MAX_N; ++n)
     b->mode[n] = n >= POLYDET_BATCH_MATERIALIZE_N ? POLYDET_BATCH_MATERIALIZED : POLYDET_BATCH_FUSED;
   update_ws(b);
+  if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) {
+    destroy_batch(b);
+    return POLYDET_ECUDA;
+  }
+  for (auto &e : b->ev) {
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      destroy_batch(b);
+      return POLYDET_ECUDA;
+    }
+  }
   for (int j = 0; j < njobs; ++j) {
     polydet_plan_s *pl = b->plans[j];
     const int k = pl->nvars;
@@ -312,23 +333,38 @@ extern "C" int polydet_batch_eval(polydet_batch_t b, const int32_t *coeffs, uint
 }
 
 // Materialized order: per job and chunk of primes, the first variable's pass
-// into the workspace, then the condensation kernel over the chunk.
+// into one of two chunk buffers, then the condensation kernel over it.  The
+// passes run on a side stream, so the pass of chunk c + 1 overlaps the
+// condensation of chunk c (filling the SMs its last wave leaves idle); a
+// buffer is refilled only after the condensation that read it.  Event
+// dependencies only: the whole sequence can be captured in a CUDA graph.
 static int condense_materialized(polydet_batch_s *b, int n, const uint32_t *partial,
                                  uint32_t *detvals, uint32_t *ws, cudaStream_t st) {
-  uint32_t *chunk = ws + kWsHead;
+  cudaStream_t sd = b->side;
+  PD_CUDA(cudaEventRecord(b->ev[4], st));  // fork
+  PD_CUDA(cudaStreamWaitEvent(sd, b->ev[4], 0));
+  int c = 0;
   for (int j : b->jobs_of[n]) {
     polydet_plan_s *pl = b->plans[j];
     const int cp = chunk_primes(b, pl);
     const EvLayout lay = pd_tail_layout(pl);
-    for (int lo = 0; lo < pl->P; lo += cp) {
+    for (int lo = 0; lo < pl->P; lo += cp, ++c) {
       const int hi = std::min(pl->P, lo + cp);
-      int rc = pd_eval_tail(pl, partial + b->part_off[j], lo, hi, chunk, lay, st);
+      const int buf = c & 1;
+      uint32_t *chunk = ws + kWsHead + (uint64_t)buf * b->chunk_max;
+      if (c >= 2) PD_CUDA(cudaStreamWaitEvent(sd, b->ev[2 + buf], 0));  // its last reader is done
+      int rc = pd_eval_tail(pl, partial + b->part_off[j], lo, hi, chunk, lay, sd);
       if (rc) return rc;
+      PD_CUDA(cudaEventRecord(b->ev[buf], sd));
+      PD_CUDA(cudaStreamWaitEvent(st, b->ev[buf], 0));
       rc = pd_launch_condense(pl, chunk, lay, lo, hi - lo, detvals + b->det_off[j] + (int64_t)lo * pl->G,
                               st);
       if (rc) return rc;
+      PD_CUDA(cudaEventRecord(b->ev[2 + buf], st));
     }
   }
+  PD_CUDA(cudaEventRecord(b->ev[5], sd));  // join
+  PD_CUDA(cudaStreamWaitEvent(st, b->ev[5], 0));
   return POLYDET_OK;
 }
 

@@ -125,7 +125,7 @@ def analytic_mode(s: Shape, mode: int) -> tuple:
         hws = max([words_after(v - 1) for v in range(2, k, 2)], default=0) * n2 * P
         Gs = binding.tail_entry_words(M)
         cp = max(1, min(P, binding.BATCH_CHUNK_WORDS // (n2 * Gs)))
-        ws = max(ws, hws, cp * n2 * Gs)
+        ws = max(ws, hws, 2 * (-(-(cp * n2 * Gs) // 64) * 64))  # two chunk buffers
         moved = 4 * (2 * mat_part + 2 * P * n2 * G + 2 * P * G + P * C + C * W)
         launches = max(1, k - 1) + 2 * (-(-P // cp)) + k + 1
     words = n2 * E + partial + P * G + P * C + C * W + 256 + ws
