@@ -22,6 +22,7 @@
 namespace {
 constexpr int kCounterWords = 2 * (POLYDET_MAX_N + 1);  // one 64-bit counter per order
 constexpr uint64_t kWsHead = 256;                       // words reserved for the counters
+constexpr int kFan = 4;                                 // streams for the per-job stages
 
 int pow2_at_least(int x) {
   int v = 1;
@@ -52,7 +53,26 @@ struct polydet_batch_s {
   // of buffer b done, ev[4] / ev[5] = fork / join
   cudaStream_t side = nullptr;
   cudaEvent_t ev[6] = {};
+  // per-job launches of stages 1, 3, 4 fan out over kFan streams (job j on
+  // fan[j % kFan], with its own scratch slice), joined back by events
+  cudaStream_t fan[kFan] = {};
+  cudaEvent_t fev[kFan + 1] = {};
+  uint64_t scratch_stride = 0;
 };
+
+static int fan_begin(polydet_batch_s *b, cudaStream_t st) {
+  PD_CUDA(cudaEventRecord(b->fev[kFan], st));
+  for (int i = 0; i < kFan; ++i) PD_CUDA(cudaStreamWaitEvent(b->fan[i], b->fev[kFan], 0));
+  return POLYDET_OK;
+}
+
+static int fan_end(polydet_batch_s *b, cudaStream_t st) {
+  for (int i = 0; i < kFan; ++i) {
+    PD_CUDA(cudaEventRecord(b->fev[i], b->fan[i]));
+    PD_CUDA(cudaStreamWaitEvent(st, b->fev[i], 0));
+  }
+  return POLYDET_OK;
+}
 
 // Primes of job `pl` per materialized chunk: as many as fit in the chunk
 // budget, at least one.
@@ -65,7 +85,7 @@ static int chunk_primes(const polydet_batch_s *b, const polydet_plan_s *pl) {
 // Workspace words for the current modes: the counters, then the largest
 // scratch any job needs in any stage (stages run one after another).
 static void update_ws(polydet_batch_s *b) {
-  uint64_t ws = 0, cmax = 0;
+  uint64_t scratch = 0, cmax = 0;
   for (int j = 0; j < b->njobs; ++j) {
     const polydet_plan_s *pl = b->plans[j];
     uint64_t need = pl->interp_ws_words * (uint64_t)pl->P;
@@ -76,11 +96,13 @@ static void update_ws(polydet_batch_s *b) {
       cmax = std::max<uint64_t>(cmax, (uint64_t)chunk_primes(b, pl) * pl->n * pl->n *
                                           (uint64_t)pd_tail_layout(pl).entry);
     }
-    ws = std::max(ws, need);
+    scratch = std::max(scratch, need);
   }
+  b->scratch_stride = (scratch + 63) / 64 * 64;
   b->chunk_max = (cmax + 63) / 64 * 64;
-  ws = std::max<uint64_t>(ws, 2 * b->chunk_max);  // two chunk buffers, filled alternately
-  b->ws_words = kWsHead + ws;
+  // stages run one after another: the fan-out scratch slices (stages 1, 3)
+  // and the two chunk buffers (stage 2) share the same words
+  b->ws_words = kWsHead + std::max<uint64_t>(kFan * b->scratch_stride, 2 * b->chunk_max);
 }
 
 static void destroy_batch(polydet_batch_s *b) {
@@ -89,7 +111,11 @@ static void destroy_batch(polydet_batch_s *b) {
   for (int n = 0; n <= POLYDET_MAX_N; ++n) cudaFree(b->d_segs[n]);
   for (auto e : b->ev)
     if (e) cudaEventDestroy(e);
+  for (auto e : b->fev)
+    if (e) cudaEventDestroy(e);
   if (b->side) cudaStreamDestroy(b->side);
+  for (auto f : b->fan)
+    if (f) cudaStreamDestroy(f);
   delete b;
 }
 
@@ -176,6 +202,18 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
   }
   for (auto &e : b->ev) {
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      destroy_batch(b);
+      return POLYDET_ECUDA;
+    }
+  }
+  for (auto &e : b->fev) {
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      destroy_batch(b);
+      return POLYDET_ECUDA;
+    }
+  }
+  for (auto &f : b->fan) {
+    if (cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking) != cudaSuccess) {
       destroy_batch(b);
       return POLYDET_ECUDA;
     }
@@ -301,12 +339,16 @@ __global__ void repack_kernel(const int32_t *__restrict__ coeffs, uint32_t *__re
 extern "C" int polydet_batch_eval_n(polydet_batch_t b, int n, const int32_t *coeffs,
                                     uint32_t *partial, uint32_t *ws, void *stream) {
   if (!b || !coeffs || !partial || !ws || n < 0 || n > POLYDET_MAX_N) return POLYDET_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
+  cudaStream_t st0 = (cudaStream_t)stream;
+  int rc = fan_begin(b, st0);
+  if (rc) return rc;
   for (int j = 0; j < b->njobs; ++j) {
     polydet_plan_s *pl = b->plans[j];
     if (n && pl->n != n) continue;
+    cudaStream_t st = b->fan[j % kFan];
+    uint32_t *scratch = ws + kWsHead + (uint64_t)(j % kFan) * b->scratch_stride;
     if (b->mode[pl->n] == POLYDET_BATCH_MATERIALIZED) {
-      int rc = pd_eval_head(pl, coeffs + b->coeff_off[j], partial + b->part_off[j], ws + kWsHead, st);
+      rc = pd_eval_head(pl, coeffs + b->coeff_off[j], partial + b->part_off[j], scratch, st);
       if (rc) return rc;
       continue;
     }
@@ -320,11 +362,11 @@ extern "C" int polydet_batch_eval_n(polydet_batch_t b, int n, const int32_t *coe
       PD_CUDA(cudaGetLastError());
       continue;
     }
-    int rc = pd_eval_partial(pl, coeffs + b->coeff_off[j], 0, pl->P, partial + b->part_off[j],
-                             b->Lp[j], ws + kWsHead, st);
+    rc = pd_eval_partial(pl, coeffs + b->coeff_off[j], 0, pl->P, partial + b->part_off[j], b->Lp[j],
+                         scratch, st);
     if (rc) return rc;
   }
-  return POLYDET_OK;
+  return fan_end(b, st0);
 }
 
 extern "C" int polydet_batch_eval(polydet_batch_t b, const int32_t *coeffs, uint32_t *partial,
@@ -400,23 +442,29 @@ extern "C" int polydet_batch_condense(polydet_batch_t b, const uint32_t *partial
 extern "C" int polydet_batch_interp(polydet_batch_t b, const uint32_t *detvals, uint32_t *residues,
                                     uint32_t *ws, void *stream) {
   if (!b || !detvals || !residues || !ws) return POLYDET_EINVAL;
+  cudaStream_t st0 = (cudaStream_t)stream;
+  int rc = fan_begin(b, st0);
+  if (rc) return rc;
   for (int j = 0; j < b->njobs; ++j) {
     polydet_plan_s *pl = b->plans[j];
-    int rc = polydet_interp(pl, detvals + b->det_off[j], 0, pl->P, residues + b->res_off[j],
-                            ws + kWsHead, stream);
+    rc = polydet_interp(pl, detvals + b->det_off[j], 0, pl->P, residues + b->res_off[j],
+                        ws + kWsHead + (uint64_t)(j % kFan) * b->scratch_stride, b->fan[j % kFan]);
     if (rc) return rc;
   }
-  return POLYDET_OK;
+  return fan_end(b, st0);
 }
 
 extern "C" int polydet_batch_crt(polydet_batch_t b, const uint32_t *residues, uint32_t *limbs,
                                  void *stream) {
   if (!b || !residues || !limbs) return POLYDET_EINVAL;
+  cudaStream_t st0 = (cudaStream_t)stream;
+  int rc = fan_begin(b, st0);
+  if (rc) return rc;
   for (int j = 0; j < b->njobs; ++j) {
-    int rc = polydet_crt(b->plans[j], residues + b->res_off[j], limbs + b->limb_off[j], stream);
+    rc = polydet_crt(b->plans[j], residues + b->res_off[j], limbs + b->limb_off[j], b->fan[j % kFan]);
     if (rc) return rc;
   }
-  return POLYDET_OK;
+  return fan_end(b, st0);
 }
 
 extern "C" int polydet_batch_sync_status(polydet_batch_t b, void *stream, uint32_t *status_out) {

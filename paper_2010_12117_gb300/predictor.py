@@ -108,7 +108,8 @@ def analytic_mode(s: Shape, mode: int) -> tuple:
         for u in range(k):
             sz *= M[u] if u < v else (D[u] + 1)
         iws = max(iws, sz)
-    ws = P * 2 * iws
+    scratch = P * 2 * iws
+    chunk = 0
     if mode == binding.BATCH_FUSED:
         pws = 0
         if k > 2:
@@ -118,16 +119,19 @@ def analytic_mode(s: Shape, mode: int) -> tuple:
                     sz *= (s.degs[u] + 1) if u < v else M[u]
                 pws = max(pws, sz)
             pws *= 2 * n2
-        ws = max(ws, P * pws)
+        scratch = max(scratch, P * pws)
         moved = 4 * (2 * fused_part + 2 * P * G + P * C + C * W)
         launches = max(1, k - 1) + k + 2
     else:
         hws = max([words_after(v - 1) for v in range(2, k, 2)], default=0) * n2 * P
         Gs = binding.tail_entry_words(M)
         cp = max(1, min(P, binding.BATCH_CHUNK_WORDS // (n2 * Gs)))
-        ws = max(ws, hws, 2 * (-(-(cp * n2 * Gs) // 64) * 64))  # two chunk buffers
+        scratch = max(scratch, hws)
+        chunk = -(-(cp * n2 * Gs) // 64) * 64
         moved = 4 * (2 * mat_part + 2 * P * n2 * G + 2 * P * G + P * C + C * W)
         launches = max(1, k - 1) + 2 * (-(-P // cp)) + k + 1
+    # the workspace: 4 fan-out scratch slices or two chunk buffers, whichever is larger
+    ws = max(4 * (-(-scratch // 64) * 64), 2 * chunk)
     words = n2 * E + partial + P * G + P * C + C * W + 256 + ws
     updates = P * G * (n - 1) * n * (2 * n - 1) // 6
     t = max(updates / UPDATE_RATE, moved / HBM_RATE) + launches * LAUNCH_S
