@@ -90,8 +90,8 @@ typedef struct polydet_plan_info {
  * and interpolate by inverse NTT, as the paper does (Sec. 3.1, 3.3).  Without
  * it the plan evaluates on the node grid: D_v + 1 distinct powers of w_v
  * (the first D_v + 1 in coset order), i.e. exactly as many nodes as the
- * degree bound needs (Sec. 2), and interpolates with the inverse of their
- * Vandermonde matrix.  Both give the
+ * degree bound needs (Sec. 2), and interpolates through them exactly (the
+ * unique polynomial of degree <= D_v, see polydet_interp).  Both give the
  * same determinant; the node grid condenses prod (D_v+1) / prod N_v as many
  * matrices. */
 #define POLYDET_FLAG_FULL_GRID 0x1u
