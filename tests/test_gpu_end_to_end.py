@@ -168,3 +168,18 @@ def test_batched_members_certified():
             assert got.coeffs == bareiss.det_packed(pm.coeffs.tolist(), pm.degs), pm.name
         else:
             assert certificate.check(pm.coeffs.tolist(), pm.degs, got.coeffs, got.D, trials=2), pm.name
+
+
+def test_six_variables_and_long_univariate_grids():
+    """The widest shapes the plan takes: six variables (the maximum), and one
+    variable with 6001 nodes (a 2x2 matrix of degree-3000 polynomials: 750
+    whole cosets of the 8th roots plus one node) against the oracle."""
+    rng = np.random.default_rng(606)
+    pm = synth.random_matrix(rng, 2, (1, 1, 1, 1, 1, 1), 0.8, -50, 50)
+    got = det(pm)
+    assert got.coeffs == bareiss.det_packed(pm.coeffs.tolist(), pm.degs)
+    pm = synth.random_matrix(rng, 2, (3000,), 1.0, -1000, 1000)
+    got = det(pm)
+    assert got.coeffs == bareiss.det_packed(pm.coeffs.tolist(), pm.degs)
+    # the full grid (8192 nodes, inverse NTT) gives the same
+    assert det(pm, full_grid=True).coeffs == got.coeffs
