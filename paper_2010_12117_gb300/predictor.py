@@ -85,20 +85,22 @@ def analytic_mode(s: Shape, mode: int) -> tuple:
     tensor sized for either mode, determinant values, residues, limbs,
     workspace) and a roofline time, max(updates / integer-pipe rate,
     bytes / HBM rate) plus a per-launch cost."""
+    from .runner import variable_order
     n, k, P = s.n, s.k, s.P
-    D = [n * d for d in s.degs]
+    degs = tuple(s.degs[v] for v in variable_order(n, s.degs))  # the batched form's order
+    D = [n * d for d in degs]
     M = [x + 1 for x in D]  # evaluation nodes per variable (node grid)
     G = math.prod(M)
     C = math.prod(x + 1 for x in D)
-    E = math.prod(d + 1 for d in s.degs)
-    L = s.degs[-1] + 1
+    E = math.prod(d + 1 for d in degs)
+    L = degs[-1] + 1
     Lp = _nextpow2(L)
     rows = G // M[-1]
     W = _limbs(P)
     n2 = n * n
 
     def words_after(v):  # per entry, after the passes of the variables > v
-        return math.prod((s.degs[u] + 1) if u <= v else M[u] for u in range(k))
+        return math.prod((degs[u] + 1) if u <= v else M[u] for u in range(k))
     fused_part = P * rows * n2 * Lp
     mat_part = P * n2 * words_after(0)
     partial = -(-max(fused_part, mat_part) // 8) * 8
@@ -116,7 +118,7 @@ def analytic_mode(s: Shape, mode: int) -> tuple:
             for v in range(1, k - 1):
                 sz = L
                 for u in range(k - 1):
-                    sz *= (s.degs[u] + 1) if u < v else M[u]
+                    sz *= (degs[u] + 1) if u < v else M[u]
                 pws = max(pws, sz)
             pws *= 2 * n2
         scratch = max(scratch, P * pws)

@@ -16,8 +16,8 @@ from typing import Dict, List, Optional, Sequence
 import numpy as np
 import torch
 
-from .binding import (BATCH_FUSED, BATCH_MATERIALIZED, EBOUND, Plan, PolydetError, as_u32,
-                      limbs_to_ints, tail_entry_words)
+from .binding import (BATCH_FUSED, BATCH_MATERIALIZE_N, BATCH_MATERIALIZED, EBOUND, Plan,
+                      PolydetError, as_u32, limbs_to_ints, tail_entry_words)
 from .pipeline import prime_count
 
 
@@ -159,6 +159,23 @@ class PlainRunner:
             pl.close()
 
 
+def variable_order(n: int, degs: Sequence[int]) -> List[int]:
+    """The order the batched form runs a job's variables in: the one of
+    lowest degree first when its matrix order is materialized by default (the
+    first variable's pass writes every evaluated matrix, and a short input is
+    the cheapest to transform), last when fused (the last variable is the
+    one evaluated inside the determinant kernel).  Ties keep the given order."""
+    order = sorted(range(len(degs)), key=lambda v: (int(degs[v]), v))
+    return order if n >= BATCH_MATERIALIZE_N else order[::-1]
+
+
+def permute_coeffs(coeffs: np.ndarray, degs: Sequence[int], order: Sequence[int]) -> np.ndarray:
+    """[n][n][E] lex coefficients with the variables taken in ``order``."""
+    n = coeffs.shape[0]
+    t = np.asarray(coeffs).reshape((n, n) + tuple(int(d) + 1 for d in degs))
+    return t.transpose((0, 1) + tuple(2 + v for v in order)).reshape(n, n, -1)
+
+
 class BatchedRunner:
     """The batched form: every job of the list in one run of four stages
     (partial evaluation; per matrix order either one persistent fused
@@ -173,7 +190,11 @@ class BatchedRunner:
         self.mats = list(mats)
         Ps = [nprimes[i] if nprimes is not None else prime_count(pm.coeffs)
               for i, pm in enumerate(self.mats)]
-        self.batch = Batch([(pm.n, pm.degs, P) for pm, P in zip(self.mats, Ps)], full_grid=full_grid)
+        # every job runs with its variables in variable_order(); results()
+        # puts the output coefficients back in the caller's order
+        self.orders = [variable_order(pm.n, pm.degs) for pm in self.mats]
+        self.batch = Batch([(pm.n, tuple(pm.degs[v] for v in o), P)
+                            for pm, o, P in zip(self.mats, self.orders, Ps)], full_grid=full_grid)
         self.dev = torch.device(device)
         w = self.batch.words
         self.coeffs_dev = torch.empty(max(1, w["coeffs"]), dtype=torch.int32, device=self.dev)
@@ -186,8 +207,8 @@ class BatchedRunner:
         self.host_out = torch.empty(max(1, w["limbs"]), dtype=torch.int32, pin_memory=True)
         co = self.batch.offsets["coeffs"]
         for i, pm in enumerate(self.mats):
-            self.host_in[co[i]:co[i + 1]] = torch.from_numpy(
-                np.ascontiguousarray(pm.coeffs, dtype=np.int32).reshape(-1))
+            c = permute_coeffs(pm.coeffs, pm.degs, self.orders[i])
+            self.host_in[co[i]:co[i + 1]] = torch.from_numpy(np.ascontiguousarray(c, dtype=np.int32).reshape(-1))
         self.graph = None
         self.tuning = {}
         st = stream or torch.cuda.current_stream()
@@ -344,7 +365,15 @@ class BatchedRunner:
         lo = self.batch.offsets["limbs"]
         for j, info in enumerate(self.batch.job_info):
             C, W = int(info.C), int(info.W)
-            out.append(limbs_to_ints(host[lo[j]:lo[j + 1]].reshape(C, W), W))
+            vals = limbs_to_ints(host[lo[j]:lo[j + 1]].reshape(C, W), W)
+            order = self.orders[j]
+            if list(order) != sorted(order):  # back to the caller's variable order
+                box = tuple(int(info.D[v]) + 1 for v in range(len(order)))
+                arr = np.empty(C, dtype=object)
+                arr[:] = vals
+                inv = [order.index(v) for v in range(len(order))]
+                vals = arr.reshape(box).transpose(inv).reshape(-1).tolist()
+            out.append(vals)
         return out
 
     def release_buffers(self) -> None:

@@ -180,3 +180,17 @@ def test_pipelined_end_to_end_runs_give_the_same_limbs(steps):
     r.check_status(st)
     assert r.results() == want
     r.close()
+
+
+def test_variable_reordering_round_trips():
+    """Jobs whose variables the batched form reorders (lowest degree first for
+    materialized orders, last for fused ones) come back in the caller's
+    variable order: equal to the plain form, which keeps the order."""
+    from paper_2010_12117_gb300.runner import variable_order
+    rng = np.random.default_rng(77)
+    mats = [synth.random_matrix(rng, 15, (3, 1, 2), 0.5, -99, 99), synth.random_matrix(rng, 6, (1, 3, 2), 0.7, -99, 99),
+            synth.random_matrix(rng, 16, (2, 1), 0.6, -99, 99), synth.random_matrix(rng, 5, (1, 2), 1.0, -9, 9)]
+    assert variable_order(15, (3, 1, 2)) == [1, 2, 0] and variable_order(6, (1, 3, 2)) == [1, 2, 0]
+    got = batched_results(mats)
+    for pm, g in zip(mats, got):
+        assert g == plain(pm), (pm.n, pm.degs)

@@ -129,11 +129,12 @@ def test_analytic_memory_is_the_layout_of_the_library(mode):
     residues, limbs, workspace)."""
     from paper_2010_12117_gb300.binding import Batch
     from paper_2010_12117_gb300.predictor import analytic, analytic_mode, shape_of
+    from paper_2010_12117_gb300.runner import variable_order
     rng = np.random.default_rng(5)
     for n, degs in [(6, (2, 1, 2)), (14, (2, 2)), (20, (1, 3, 1)), (16, (4,))]:
         pm = synth.random_matrix(rng, n, degs, 0.5, -99, 99)
         s = shape_of(pm)
-        b = Batch([(n, degs, s.P)])
+        b = Batch([(n, tuple(degs[v] for v in variable_order(n, degs)), s.P)])  # as the runner plans it
         b.set_mode(n, mode)
         words = sum(b.words.values())
         b.close()
