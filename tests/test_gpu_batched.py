@@ -194,3 +194,38 @@ def test_variable_reordering_round_trips():
     got = batched_results(mats)
     for pm, g in zip(mats, got):
         assert g == plain(pm), (pm.n, pm.degs)
+
+
+def test_batch_api_rejects_bad_settings():
+    from paper_2010_12117_gb300.binding import BATCH_FUSED, Batch, PolydetError
+    b = Batch([(5, (1, 2), 3), (16, (2,), 4)])
+    try:
+        with pytest.raises(PolydetError):
+            b.set_mode(5, 7)
+        with pytest.raises(PolydetError):
+            b.set_mode(0, BATCH_FUSED)
+        with pytest.raises(PolydetError):
+            b.set_chunk_words(0)
+        with pytest.raises(PolydetError):
+            b.set_launch(16, 48)  # not a multiple of 32
+        assert b.mode(5) == BATCH_FUSED and b.mode(16) == 1
+        w0 = b.words["workspace"]
+        b.set_chunk_words(1)  # one prime per chunk: the workspace shrinks or stays
+        assert b.words["workspace"] <= w0
+    finally:
+        b.close()
+
+
+def test_one_by_one_and_constant_jobs_in_both_modes():
+    """Degenerate jobs: 1x1 matrices (the entry itself) and constant entries
+    (degree 0 in every variable), fused and materialized."""
+    from paper_2010_12117_gb300.binding import BATCH_FUSED, BATCH_MATERIALIZED
+    rng = np.random.default_rng(3)
+    mats = [synth.PolyMatrix(1, (3, 2), np.arange(12, dtype=np.int64).reshape(1, 1, 12) - 6),
+            synth.random_matrix(rng, 4, (0,), 1.0, -9, 9), synth.random_matrix(rng, 15, (0, 0), 1.0, -9, 9),
+            synth.random_matrix(rng, 3, (2, 0, 1), 0.9, -9, 9)]
+    for mode in (BATCH_FUSED, BATCH_MATERIALIZED):
+        got = batched_results(mats, modes=mode)
+        assert got[0] == mats[0].coeffs[0, 0].tolist()
+        for pm, g in zip(mats[1:], got[1:]):
+            assert g == plain(pm), (mode, pm.n, pm.degs)
