@@ -2,10 +2,10 @@
 //
 // A team of T consecutive lanes owns one matrix: lane t holds the columns
 // j = t, t + T, t + 2T, ... entirely in registers (one lane for n <= 15,
-// up to 16 lanes at n = 32).  Every index into the register array
-// is a compile-time constant after unrolling (see TeamFor for the lanes per
-// matrix of each order), so nothing spills to local
-// memory, and there are no barriers: the team talks through warp shuffles.
+// up to 16 lanes at n = 32; the per-order T and the CTAs per SM the kernel is
+// compiled for are the table of teams.cuh).  Every index into the register
+// array is a compile-time constant after unrolling, and there are no
+// barriers: the team talks through warp shuffles.
 //
 // Elimination is fraction free (the paper's update, Algorithm 3 step (3)):
 // at step c every column j > c of every row i > c becomes
@@ -17,11 +17,13 @@
 // as prod_{c<n-1} Q_c with Q_c = prod_{j<=c} v_jj, and inverted once by
 // Fermat's little theorem at the end, instead of one inverse per step.
 //
-// Pivot search (Algorithm 3, lines 4-7: first nonzero entry): when the
-// pivot a_cc is zero, the first row r > c with a_rc != 0 is added to row c,
-// which leaves the determinant unchanged.  If the column is zero below c the
-// pivot stays 0 and the result is 0, as the paper states.  The search runs
-// only when some lane of the warp needs it.
+// Pivot search (Algorithm 3's first nonzero entry): when the pivot a_cc is
+// zero, the first row r > c with a_rc != 0 is added to row c, which leaves
+// the determinant unchanged.  If the column is zero below c the pivot stays 0
+// and the result is 0, as the paper states.  The elimination first runs
+// without any search (no warp vote per step); a zero pivot is only recorded,
+// and the rare warp that met one redoes its matrices with the search
+// (ElimStep, out of line).
 #pragma once
 
 #include "common.cuh"

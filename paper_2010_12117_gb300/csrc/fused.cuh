@@ -16,8 +16,8 @@
 // item:
 //  0. the CTA copies the Q rows its nodes need (about S / M_k + 1) into
 //     shared memory with coalesced 16-byte loads;
-//  1. a team of T lanes owns node g = (row, i): it forms x = w_k^i
-//     (Montgomery form, from the twiddle table) and its powers, and evaluates
+//  1. a team of T lanes owns node g = (row, i): it forms x, the node's power
+//     of w_k (Montgomery form, from the twiddle table) and its powers, and evaluates
 //     each entry of its columns, sum_l Q[row][entry][l] x^l, with one REDC per
 //     two products (2 p^2 < p 2^32), into its own slice of shared memory
 //     (rolled loops: small code, no register pressure);
