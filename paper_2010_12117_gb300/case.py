@@ -22,9 +22,16 @@ def main(argv=None) -> int:
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--mode", choices=("default", "fused", "materialized"), default="default")
     ap.add_argument("--chunk-words", type=int, default=0, help="materialized chunk budget (0: default)")
+    ap.add_argument("--stage", choices=("det", "eval", "crt"), default="det",
+                    help="det: the whole job in both forms; eval: the evaluation of the 12x12 "
+                         "trivariate workload alone; crt: the CRT of 2^24 coefficients alone")
+    ap.add_argument("--primes", type=int, default=5, help="primes for --stage eval / crt")
+    ap.add_argument("--full-grid", action="store_true", help="--stage eval on the power-of-two grid")
     args = ap.parse_args(argv)
 
     import torch
+    if args.stage != "det":
+        return _stage(args)
     from . import synth
     from .binding import BATCH_FUSED, BATCH_MATERIALIZED
     from .runner import BatchedRunner, PlainRunner
@@ -59,6 +66,36 @@ def main(argv=None) -> int:
     if got != want:
         print("MISMATCH between the plain and the batched form", sizes)
         return 1
+    print("ok", sizes)
+    return 0
+
+
+def _stage(args) -> int:
+    """One stage alone, twice (a warm-up launch and one to profile)."""
+    import torch
+    from . import synth
+    from .binding import Plan
+    st = torch.cuda.Stream()
+    P = args.primes
+    if args.stage == "eval":
+        pm = synth.sparse_12x12_xyz(0)
+        pl = Plan(pm.n, pm.degs, P, full_grid=args.full_grid)
+        c = torch.from_numpy(pm.coeffs.astype(np.int32).reshape(-1)).cuda()
+        ev = torch.empty(P * pm.n * pm.n * pl.G, dtype=torch.int32, device="cuda")
+        ws = pl.workspace(P)
+        for _ in range(2):
+            pl.eval(c, 0, P, ev, ws, st)
+        sizes = f"eval 12x12 over Z[x,y,z], G={pl.G}, P={P}, {4 * ev.numel() / 1e6:.0f} MB written"
+    else:
+        pl = Plan(1, (4095, 4095), P)  # C = 4096^2 coefficients
+        g = torch.Generator(device="cuda").manual_seed(args.seed)
+        res = torch.randint(0, 2 ** 30, (P * pl.C,), dtype=torch.int32, device="cuda", generator=g)
+        limbs = torch.empty(pl.C * pl.W, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            pl.crt(res, limbs, st)
+        sizes = f"crt of C={pl.C} coefficients, P={P}, W={pl.W}"
+    st.synchronize()
+    pl.close()
     print("ok", sizes)
     return 0
 
