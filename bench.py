@@ -296,7 +296,7 @@ def served_leg(args, mats, batched_value, st):
     return out
 
 
-def kernel_leg(st, hbm_peak):
+def kernel_leg(st, hbm_peak, mats):
     """Stages alone on inputs larger than L2 (the 12x12 trivariate workload):
     evaluation on the node grid (37^3 nodes, 20 primes: 583 MB written) and on
     the paper's full grid (64^3 nodes, 5 primes: 755 MB), interpolation on
@@ -356,11 +356,63 @@ def kernel_leg(st, hbm_peak):
         limbs = torch.empty(C * pc.W, dtype=torch.int32, device="cuda")
         ms = timed(lambda: pc.crt(res, limbs, st))
         byts = 4.0 * C * (P + pc.W)
-        out[f"crt_2^24_P{P}"] = dict(hbm(ms, byts), W=pc.W)
+        W = pc.W
+        # the integer side: Garner P (P - 1) / 2 mulmods and P W limb products
+        mulmods = float(C) * (P * (P - 1) / 2 + P * W)
+        out[f"crt_2^24_P{P}"] = dict(hbm(ms, byts), W=W, mulmods_per_s=mulmods / (ms * 1e-3))
         pc.close()
         del res, limbs
     torch.cuda.empty_cache()
+    out["eval_batched_workload"] = eval_totals(mats, st, hbm_peak)
+    torch.cuda.empty_cache()
     return out
+
+
+def eval_totals(mats, st, hbm_peak):
+    """The evaluation (every NTT pass) of every job of the batched workload,
+    one job after another through the per-matrix API, in the variable order
+    the batched form uses: aggregate algorithmic bytes (int32 coefficients in,
+    evaluated matrices out) over the sum of the launches' event times."""
+    import numpy as np
+    import torch
+    from paper_2010_12117_gb300.binding import Plan
+    from paper_2010_12117_gb300.pipeline import prime_count
+    from paper_2010_12117_gb300.runner import permute_coeffs, variable_order
+    budget = 1 << 29  # words of evaluated matrices per launch group
+    plans = []
+    most, ws_most = budget, 1
+    for pm in mats:
+        order = variable_order(pm.n, pm.degs)
+        degs = tuple(pm.degs[v] for v in order)
+        pl = Plan(pm.n, degs, prime_count(pm.coeffs))
+        c = torch.from_numpy(np.ascontiguousarray(permute_coeffs(pm.coeffs, pm.degs, order),
+                                                  dtype=np.int32).reshape(-1)).cuda()
+        per = pm.n * pm.n * pl.G
+        cp = max(1, min(pl.P, budget // per))
+        most = max(most, cp * per)
+        ws_most = max(ws_most, cp * pl.eval_ws_words)
+        plans.append((pm, pl, c, cp))
+    buf = torch.empty(most, dtype=torch.int32, device="cuda")
+    wsb = torch.empty(ws_most, dtype=torch.int32, device="cuda")
+    ms_total, byts = 0.0, 0.0
+    for rep in range(2):  # the first pass warms up
+        evs = []
+        for pm, pl, c, cp in plans:
+            for lo in range(0, pl.P, cp):
+                hi = min(pl.P, lo + cp)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                pl.eval(c, lo, hi, buf, wsb, st)
+                b.record(st)
+                evs.append((a, b, 4.0 * (hi - lo) * pm.n * pm.n * (pl.E + pl.G)))
+        st.synchronize()
+        if rep:
+            ms_total = sum(a.elapsed_time(b) for a, b, _ in evs)
+            byts = sum(x for _, _, x in evs)
+    for _, pl, _, _ in plans:
+        pl.close()
+    return {"ms": ms_total, "GBps": byts / ms_total / 1e6, "frac": byts / ms_total / 1e6 / hbm_peak,
+            "algorithmic_bytes": byts, "bound": "hbm", "launch_groups": len(evs)}
 
 
 def run_ours(args, world, rank, local):
@@ -501,7 +553,7 @@ def run_ours(args, world, rank, local):
                       "same kernel)")
 
     served = None if args.no_served else served_leg(args, mats, value, st)
-    kernels = None if args.no_kernels else kernel_leg(st, hbm_peak)
+    kernels = None if args.no_kernels else kernel_leg(st, hbm_peak, mats)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
