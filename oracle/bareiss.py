@@ -15,6 +15,8 @@ determinant directly, with no modular arithmetic at all:
   workload reachable in Python.
 * ``det_leibniz_poly``: the permutation expansion, for n <= 5 (a route that
   shares nothing with elimination).
+* ``det_bareiss``: O1 for a matrix given entry by entry (dicts or dense
+  coefficient arrays), returning the dense coefficient array of the result.
 """
 from __future__ import annotations
 
@@ -193,3 +195,42 @@ def det_poly_dense(coeffs, degs: Sequence[int]) -> List[int]:
     M = P.matrix_from_dense(coeffs, degs)
     det = det_bareiss_poly(M, k)
     return P.to_dense(det, det_degree_bound(n, degs))
+
+
+def det_bareiss(M) -> "np.ndarray":
+    """O1 on a matrix given entry by entry, returning the determinant as a
+    dense object array of Python ints with shape (D_1+1, ..., D_k+1), index
+    (e_1, ..., e_k) the exponent vector (D_v = n * d_v, Sec. 2).
+
+    Each entry of ``M`` is either a dict {exponent tuple: int} or an integer
+    array of shape (d_1+1, ..., d_k+1) indexed by the exponent vector; the
+    number of variables k and the degrees d_v are read off the entries (the
+    largest exponent of x_v over all entries)."""
+    import numpy as np
+    n = len(M)
+    k = 0
+    for row in M:
+        for e in row:
+            if isinstance(e, dict):
+                k = max(k, max((len(x) for x in e), default=0))
+            else:
+                k = max(k, np.asarray(e).ndim)
+    k = max(k, 1)
+    polys = []
+    for row in M:
+        prow = []
+        for e in row:
+            if isinstance(e, dict):
+                prow.append({tuple(x) + (0,) * (k - len(x)): int(c) for x, c in e.items() if c})
+            else:
+                a = np.asarray(e)
+                a = a.reshape(a.shape + (1,) * (k - a.ndim))
+                prow.append({tuple(int(i) for i in idx): int(c) for idx, c in np.ndenumerate(a) if c})
+        polys.append(prow)
+    degs = [max((x[v] for row in polys for e in row for x in e), default=0) for v in range(k)]
+    D = det_degree_bound(n, degs)
+    out = np.zeros([d + 1 for d in D], dtype=object)
+    det = det_bareiss_poly(polys, k) if n else P.const(1, k)
+    for x, c in det.items():
+        out[x] = c
+    return out

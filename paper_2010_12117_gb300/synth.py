@@ -179,3 +179,23 @@ WORKLOADS = {
     "sylvester_16_x": sylvester_16,
     "sparse_12x12_xyz": sparse_12x12_xyz,
 }
+
+
+def gen_config(i: int, seed: int, **kw):
+    """The seeded input of one of the five workloads, by index: 0 the dense
+    4x4 over Z[x, y], 1 the 16x16 Sylvester matrix, 2 the sparse 12x12 over
+    Z[x, y, z] (each a PolyMatrix), 3 the batched list of ``count`` (default
+    256) matrices, 4 the served stream of ``njobs`` (default 300) Poisson
+    arrivals at ``rate`` jobs/s (default 700)."""
+    if i == 0:
+        return dense_4x4(seed)
+    if i == 1:
+        return sylvester_16(seed)
+    if i == 2:
+        return sparse_12x12_xyz(seed)
+    if i == 3:
+        return batched(seed, kw.get("count", 256))
+    if i == 4:
+        return served_stream(seed, kw.get("njobs", 300), kw.get("rate", 700.0),
+                             kw.get("large_frac", 0.05))
+    raise ValueError(f"no workload with index {i}")

@@ -440,3 +440,40 @@ def test_node_grid_interpolation_on_coset_ordered_nodes():
             for g in range(prod(Ms))]
     assert modular.interp_nodes(vals, Ms, ws, p, exps) == vec
     assert modular.interp_nodes(vals, Ms, ws, p) != vec
+
+
+def test_det_bareiss_entry_forms_closed_forms():
+    # [[x, y], [y, x]] over Z[x, y]: det = x^2 - y^2, given as dicts
+    x, y = {(1, 0): 1}, {(0, 1): 1}
+    d = bareiss.det_bareiss([[x, y], [y, x]])
+    assert d.shape == (3, 3)
+    want = np.zeros((3, 3), dtype=object)
+    want[2, 0], want[0, 2] = 1, -1
+    assert (d == want).all()
+    # the same matrix as dense coefficient arrays indexed by the exponent vector
+    ax = np.array([[0, 0], [1, 0]])
+    ay = np.array([[0, 1], [0, 0]])
+    assert (bareiss.det_bareiss([[ax, ay], [ay, ax]]) == want).all()
+    # diag(1 + t, 2 - t, 3) over Z[t]: (1 + t)(2 - t) 3 = 6 + 3t - 3t^2
+    z = np.array([0, 0])
+    M = [[np.array([1, 1]), z, z], [z, np.array([2, -1]), z], [z, z, np.array([3, 0])]]
+    assert bareiss.det_bareiss(M).tolist() == [6, 3, -3, 0]
+
+
+def test_det_bareiss_agrees_with_leibniz_on_seeded_dense_input():
+    pm = synth.gen_config(0, 3)
+    M = [[pm.entry(i, j) for j in range(pm.n)] for i in range(pm.n)]
+    d = bareiss.det_bareiss(M)
+    Mp = P.matrix_from_dense(pm.coeffs.tolist(), pm.degs)
+    want = P.to_dense(bareiss.det_leibniz_poly(Mp, 2), plan.det_degree_bound(pm.n, pm.degs))
+    assert d.reshape(-1).tolist() == want
+
+
+def test_gen_config_indices():
+    assert synth.gen_config(0, 1).n == 4 and synth.gen_config(1, 1).n == 16
+    assert synth.gen_config(2, 1).degs == (3, 3, 3)
+    assert len(synth.gen_config(3, 1, count=5)) == 5
+    s = synth.gen_config(4, 1, njobs=20, rate=100.0)
+    assert len(s) == 20 and all(a.t < b.t for a, b in zip(s, s[1:]))
+    with pytest.raises(ValueError):
+        synth.gen_config(5, 1)
