@@ -547,6 +547,9 @@ def run_ours(args, world, rank, local):
     plain_stage_ms = ptimer.ms()
     # algorithmic bytes of the condensation launches: 4 n^2 + 4 per determinant
     cond_bytes = sum(float(pl.P * pl.G) * (4 * pm.n * pm.n + 4) for pm, pl in zip(plain.mats, plain.plans))
+    bytes_by_order = {}
+    for pm, pl in zip(plain.mats, plain.plans):
+        bytes_by_order[pm.n] = bytes_by_order.get(pm.n, 0.0) + float(pl.P * pl.G) * (4 * pm.n * pm.n + 4)
     plain.close()
     del plain
 
@@ -581,6 +584,21 @@ def run_ours(args, world, rank, local):
     plain_roofs = roofs_of(plain_stage_ms, dict(ptimer.work))
     # the dominant kernel: the condensation kernel, timed launch by launch
     nl = ptimer.launches["condense"]
+    # per order: the update rate against the integer-pipe peak, the byte rate
+    # against HBM, and the time either bound alone allows; the sum of those
+    # times over the sum of the measured ones is the kernel's fraction of its
+    # launch-by-launch roofline (small orders read 4 n^2 bytes for only
+    # (n-1) n (2n-1) / 6 updates and are HBM-bound)
+    by_order, t_bound, t_meas = {}, 0.0, 0.0
+    for n_, (ms_, upd) in sorted(ptimer.tag_ms("condense").items()):
+        byt = bytes_by_order[n_]
+        tb = max(upd / derived_upd, byt / (hbm_peak * 1e9))
+        t_bound += tb
+        t_meas += ms_ * 1e-3
+        by_order[str(n_)] = {"ms": ms_, "Gupdate_s": upd / (ms_ * 1e-3) / 1e9,
+                             "alu_frac": upd / (ms_ * 1e-3) / derived_upd,
+                             "hbm_frac": byt / (ms_ * 1e-3) / (hbm_peak * 1e9),
+                             "bound": "alu" if upd / derived_upd >= byt / (hbm_peak * 1e9) else "hbm"}
     ratio = _traffic_ratio()
     roof = dict(plain_roofs["condense"], kernel="condense_kernel", launches=nl,
                 avg_launch_ms=plain_stage_ms["condense"] / max(1, nl),
@@ -590,6 +608,8 @@ def run_ours(args, world, rank, local):
                 traffic_src=("ncu read + write / algorithmic bytes of the n = 24 capture, scaled to "
                              "the average launch" if ratio is not None else
                              "sources changed since the ncu capture"),
+                by_order=by_order,
+                frac_of_launch_bound=t_bound / t_meas if t_meas else None,
                 timed="CUDA events around each of its launches on the launching stream, plain "
                       "pass over the same batch (the batched form's materialized orders run the "
                       "same kernel)")

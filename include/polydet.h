@@ -210,7 +210,9 @@ int polydet_sync_status(polydet_plan_t plan, void *stream, uint32_t *status_out)
  *   POLYDET_BATCH_FUSED: evaluation of the last variable is fused into the
  *     determinant kernel, so evaluated matrices never reach memory: one
  *     persistent kernel per order takes (job, prime, node-block) items from
- *     a counter kept in the caller's workspace;
+ *     a counter kept in the caller's workspace, and the bulk-copy engine
+ *     (cp.async.bulk on an mbarrier) stages the next item's rows of the
+ *     partial tensor in shared memory while the current item is computed;
  *   POLYDET_BATCH_MATERIALIZED: the first variable's NTT pass writes the
  *     evaluated matrices of a chunk of primes into one of two workspace
  *     buffers and the condensation kernel of polydet_condense_batch reads
@@ -291,6 +293,14 @@ int polydet_batch_set_mode(polydet_batch_t batch, int n, int mode);
 /* Chunk budget of the materialized mode in words (>= 1; the workspace size
  * changes: query again).  Not during a graph capture. */
 int polydet_batch_set_chunk_words(polydet_batch_t batch, uint64_t words);
+/* Test hook for failure detection, off by default.  With on = 1 the fused
+ * kernels withhold the bulk copies of their staged rows (those that would be
+ * issued), so each CTA's bounded wait for them runs out after about one
+ * second; the CTA then sets POLYDET_STATUS_TIMEOUT in its job plan's status
+ * word (polydet_batch_sync_status returns POLYDET_ETIMEOUT) and ends, and the
+ * determinant values of those items are not written.  on = 0 restores normal
+ * operation.  Not during a graph capture (uploads the segment tables). */
+int polydet_batch_test_drop_copies(polydet_batch_t batch, int on);
 /* Lanes that share one determinant in the condensation kernels of order n
  * (a CTA size must be a multiple of it); POLYDET_EINVAL outside 1..32.  Host
  * only: no device call. */

@@ -98,6 +98,7 @@ SIGNATURES = {
     "polydet_batch_set_mode": (_I, [_VP, _I, _I]),
     "polydet_batch_set_chunk_words": (_I, [_VP, ctypes.c_uint64]),
     "polydet_team_size": (_I, [_I]),
+    "polydet_batch_test_drop_copies": (_I, [_VP, _I]),
     "polydet_batch_eval": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "polydet_batch_eval_n": (_I, [_VP, _I, _VP, _VP, _VP, _VP]),
     "polydet_batch_condense": (_I, [_VP, _VP, _VP, _VP, _VP]),
@@ -367,6 +368,12 @@ class Batch:
         """Budget (words) of one materialized chunk; at least one prime."""
         _check(lib().polydet_batch_set_chunk_words(self._h, int(words)), "polydet_batch_set_chunk_words")
         self.refresh()
+
+    def test_drop_copies(self, on: bool) -> None:
+        """Failure-detection test hook: withhold the fused kernels' bulk
+        copies so that their bounded waits run out (status TIMEOUT)."""
+        _check(lib().polydet_batch_test_drop_copies(self._h, int(bool(on))),
+               "polydet_batch_test_drop_copies")
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

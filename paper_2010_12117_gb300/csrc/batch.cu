@@ -42,6 +42,7 @@ struct polydet_batch_s {
   int blocks[POLYDET_MAX_N + 1] = {};
   int64_t nitems[POLYDET_MAX_N + 1] = {};
   size_t qwords[POLYDET_MAX_N + 1] = {};
+  int nbuf[POLYDET_MAX_N + 1] = {};  // buffers of staged rows per fused CTA (2, or 1 where 2 do not fit)
   std::vector<FusedSeg> segs[POLYDET_MAX_N + 1];
   FusedSeg *d_segs[POLYDET_MAX_N + 1] = {};
   int mode[POLYDET_MAX_N + 1] = {};
@@ -136,11 +137,18 @@ static int build_class(polydet_batch_s *b, int n) {
     const int64_t rows = std::min<int64_t>((S + s.Mk - 1) / s.Mk + 1, (s.G + s.Mk - 1) / s.Mk);
     qw = std::max<size_t>(qw, (size_t)rows * n * n * s.Lp);
   }
+  qw = (qw + 3) / 4 * 4;  // both buffers start on 16 bytes
   b->qwords[n] = qw;
-  int bps = 0;
-  int rc = pd_fused_occupancy(n, b->threads[n], qw, &bps);
+  int bps = 0, nbuf = 2;
+  int rc = pd_fused_occupancy(n, b->threads[n], qw, nbuf, &bps);
   if (rc) return rc;
+  if (bps < 1) {  // no room to prefetch: one buffer, the next item's copy after the current item
+    nbuf = 1;
+    rc = pd_fused_occupancy(n, b->threads[n], qw, nbuf, &bps);
+    if (rc) return rc;
+  }
   if (bps < 1) return POLYDET_EINVAL;  // the CTA's shared memory does not fit
+  b->nbuf[n] = nbuf;
   b->blocks[n] = (int)std::min<int64_t>(it, (int64_t)bps * b->sms);
   if (!b->d_segs[n]) PD_CUDA(cudaMalloc((void **)&b->d_segs[n], v.size() * sizeof(FusedSeg)));
   PD_CUDA(cudaMemcpy(b->d_segs[n], v.data(), v.size() * sizeof(FusedSeg), cudaMemcpyHostToDevice));
@@ -236,6 +244,7 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
       s.L = pl->d[k - 1] + 1;
       s.Lp = b->Lp[j];
       s.LPk = pl->LPo[k - 1];
+      s.status = pl->d_status;
       b->segs[pl->n].push_back(s);
     }
   }
@@ -248,6 +257,17 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
     }
   }
   *out = b;
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_batch_test_drop_copies(polydet_batch_t b, int on) {
+  if (!b || (on != 0 && on != 1)) return POLYDET_EINVAL;
+  for (int n = 1; n <= POLYDET_MAX_N; ++n) {
+    if (b->segs[n].empty()) continue;
+    for (auto &s : b->segs[n]) s.drop_copies = on;
+    int rc = build_class(b, n);
+    if (rc) return rc;
+  }
   return POLYDET_OK;
 }
 
@@ -428,7 +448,7 @@ extern "C" int polydet_batch_condense_n(polydet_batch_t b, int n, const uint32_t
       continue;
     }
     int rc = pd_fused_launch(m, b->d_segs[m], (int)b->segs[m].size(), b->nitems[m], partial,
-                             detvals, counters + m, b->threads[m], b->blocks[m], b->qwords[m], st);
+                             detvals, counters + m, b->threads[m], b->blocks[m], b->qwords[m], b->nbuf[m], st);
     if (rc) return rc;
   }
   return POLYDET_OK;

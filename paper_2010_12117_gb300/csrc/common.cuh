@@ -133,13 +133,17 @@ struct FusedSeg {
   int32_t Mk;          // nodes of the last variable (M_k): node g = row * Mk + i
   int32_t L, Lp;       // coefficients of x_k per entry, stride of the partial tensor
   int32_t LPk;         // node order radix of the last variable (node_exp)
+  uint32_t *status;    // the job plan's device status word
+  int32_t drop_copies; // test hook: issue no bulk copy for this segment's items
 };
 
 int pd_fused_launch(int n, const FusedSeg *segs, int nsegs, int64_t nitems, const uint32_t *partial,
                     uint32_t *detvals, unsigned long long *counter, int threads, int blocks,
-                    size_t qwords, cudaStream_t st);
-// qwords: words of partial-tensor rows one CTA stages (rows per item x n^2 x Lp)
-int pd_fused_occupancy(int n, int threads, size_t qwords, int *blocks_per_sm);
+                    size_t qwords, int nbuf, cudaStream_t st);
+// qwords: words of partial-tensor rows one item can span (rows per item x n^2 x
+// Lp, rounded up to a multiple of 4); a CTA holds nbuf (2, or 1 where two do
+// not fit) such buffers
+int pd_fused_occupancy(int n, int threads, size_t qwords, int nbuf, int *blocks_per_sm);
 int pd_fused_team(int n);
 
 // Node exponent of node k of a variable with N points and order radix L

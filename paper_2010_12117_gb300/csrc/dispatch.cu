@@ -11,29 +11,29 @@ int pd_condense_from_21(const polydet_plan_s *, const uint32_t *, EvLayout, int,
 int pd_condense_from_25(const polydet_plan_s *, const uint32_t *, EvLayout, int, int, uint32_t *, cudaStream_t);
 int pd_condense_from_29(const polydet_plan_s *, const uint32_t *, EvLayout, int, int, uint32_t *, cudaStream_t);
 int pd_fused_from_1(int, const FusedSeg *, int, int64_t, const uint32_t *, uint32_t *,
-                   unsigned long long *, int, int, size_t, cudaStream_t);
-int pd_fused_occ_from_1(int, int, size_t, int *);
+                   unsigned long long *, int, int, size_t, int, cudaStream_t);
+int pd_fused_occ_from_1(int, int, size_t, int, int *);
 int pd_fused_from_7(int, const FusedSeg *, int, int64_t, const uint32_t *, uint32_t *,
-                   unsigned long long *, int, int, size_t, cudaStream_t);
-int pd_fused_occ_from_7(int, int, size_t, int *);
+                   unsigned long long *, int, int, size_t, int, cudaStream_t);
+int pd_fused_occ_from_7(int, int, size_t, int, int *);
 int pd_fused_from_11(int, const FusedSeg *, int, int64_t, const uint32_t *, uint32_t *,
-                   unsigned long long *, int, int, size_t, cudaStream_t);
-int pd_fused_occ_from_11(int, int, size_t, int *);
+                   unsigned long long *, int, int, size_t, int, cudaStream_t);
+int pd_fused_occ_from_11(int, int, size_t, int, int *);
 int pd_fused_from_13(int, const FusedSeg *, int, int64_t, const uint32_t *, uint32_t *,
-                   unsigned long long *, int, int, size_t, cudaStream_t);
-int pd_fused_occ_from_13(int, int, size_t, int *);
+                   unsigned long long *, int, int, size_t, int, cudaStream_t);
+int pd_fused_occ_from_13(int, int, size_t, int, int *);
 int pd_fused_from_17(int, const FusedSeg *, int, int64_t, const uint32_t *, uint32_t *,
-                   unsigned long long *, int, int, size_t, cudaStream_t);
-int pd_fused_occ_from_17(int, int, size_t, int *);
+                   unsigned long long *, int, int, size_t, int, cudaStream_t);
+int pd_fused_occ_from_17(int, int, size_t, int, int *);
 int pd_fused_from_21(int, const FusedSeg *, int, int64_t, const uint32_t *, uint32_t *,
-                   unsigned long long *, int, int, size_t, cudaStream_t);
-int pd_fused_occ_from_21(int, int, size_t, int *);
+                   unsigned long long *, int, int, size_t, int, cudaStream_t);
+int pd_fused_occ_from_21(int, int, size_t, int, int *);
 int pd_fused_from_25(int, const FusedSeg *, int, int64_t, const uint32_t *, uint32_t *,
-                   unsigned long long *, int, int, size_t, cudaStream_t);
-int pd_fused_occ_from_25(int, int, size_t, int *);
+                   unsigned long long *, int, int, size_t, int, cudaStream_t);
+int pd_fused_occ_from_25(int, int, size_t, int, int *);
 int pd_fused_from_29(int, const FusedSeg *, int, int64_t, const uint32_t *, uint32_t *,
-                   unsigned long long *, int, int, size_t, cudaStream_t);
-int pd_fused_occ_from_29(int, int, size_t, int *);
+                   unsigned long long *, int, int, size_t, int, cudaStream_t);
+int pd_fused_occ_from_29(int, int, size_t, int, int *);
 
 int pd_launch_condense(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay, int prime_lo,
                        int nprimes, uint32_t *detvals, cudaStream_t st) {
@@ -52,29 +52,29 @@ int pd_launch_condense(const polydet_plan_s *pl, const uint32_t *evals, EvLayout
 
 int pd_fused_launch(int n, const FusedSeg *segs, int nsegs, int64_t nitems, const uint32_t *partial,
                     uint32_t *detvals, unsigned long long *counter, int threads, int blocks,
-                    size_t qwords, cudaStream_t st) {
+                    size_t qwords, int nbuf, cudaStream_t st) {
   if (n < 1) return POLYDET_EINVAL;
-  if (n <= 6) return pd_fused_from_1(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, st);
-  if (n <= 10) return pd_fused_from_7(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, st);
-  if (n <= 12) return pd_fused_from_11(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, st);
-  if (n <= 16) return pd_fused_from_13(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, st);
-  if (n <= 20) return pd_fused_from_17(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, st);
-  if (n <= 24) return pd_fused_from_21(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, st);
-  if (n <= 28) return pd_fused_from_25(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, st);
-  if (n <= 32) return pd_fused_from_29(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, st);
+  if (n <= 6) return pd_fused_from_1(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, nbuf, st);
+  if (n <= 10) return pd_fused_from_7(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, nbuf, st);
+  if (n <= 12) return pd_fused_from_11(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, nbuf, st);
+  if (n <= 16) return pd_fused_from_13(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, nbuf, st);
+  if (n <= 20) return pd_fused_from_17(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, nbuf, st);
+  if (n <= 24) return pd_fused_from_21(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, nbuf, st);
+  if (n <= 28) return pd_fused_from_25(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, nbuf, st);
+  if (n <= 32) return pd_fused_from_29(n, segs, nsegs, nitems, partial, detvals, counter, threads, blocks, qwords, nbuf, st);
   return POLYDET_EINVAL;
 }
 
-int pd_fused_occupancy(int n, int threads, size_t qwords, int *bps) {
+int pd_fused_occupancy(int n, int threads, size_t qwords, int nbuf, int *bps) {
   if (n < 1) return POLYDET_EINVAL;
-  if (n <= 6) return pd_fused_occ_from_1(n, threads, qwords, bps);
-  if (n <= 10) return pd_fused_occ_from_7(n, threads, qwords, bps);
-  if (n <= 12) return pd_fused_occ_from_11(n, threads, qwords, bps);
-  if (n <= 16) return pd_fused_occ_from_13(n, threads, qwords, bps);
-  if (n <= 20) return pd_fused_occ_from_17(n, threads, qwords, bps);
-  if (n <= 24) return pd_fused_occ_from_21(n, threads, qwords, bps);
-  if (n <= 28) return pd_fused_occ_from_25(n, threads, qwords, bps);
-  if (n <= 32) return pd_fused_occ_from_29(n, threads, qwords, bps);
+  if (n <= 6) return pd_fused_occ_from_1(n, threads, qwords, nbuf, bps);
+  if (n <= 10) return pd_fused_occ_from_7(n, threads, qwords, nbuf, bps);
+  if (n <= 12) return pd_fused_occ_from_11(n, threads, qwords, nbuf, bps);
+  if (n <= 16) return pd_fused_occ_from_13(n, threads, qwords, nbuf, bps);
+  if (n <= 20) return pd_fused_occ_from_17(n, threads, qwords, nbuf, bps);
+  if (n <= 24) return pd_fused_occ_from_21(n, threads, qwords, nbuf, bps);
+  if (n <= 28) return pd_fused_occ_from_25(n, threads, qwords, nbuf, bps);
+  if (n <= 32) return pd_fused_occ_from_29(n, threads, qwords, nbuf, bps);
   return POLYDET_EINVAL;
 }
 

@@ -14,8 +14,12 @@
 // in global memory until the list is exhausted, so one launch covers every
 // (job, prime) pair of a matrix order, whatever the mix of grid sizes.  Per
 // item:
-//  0. the CTA copies the Q rows its nodes need (about S / M_k + 1) into
-//     shared memory with coalesced 16-byte loads;
+//  0. the Q rows its nodes need (about S / M_k + 1, contiguous) reach shared
+//     memory by one bulk copy that thread 0 started while the CTA computed
+//     the previous item (two buffers, one mbarrier each; a wait that runs
+//     out after a second sets POLYDET_STATUS_TIMEOUT and ends the CTA).
+//     Rows whose start or size is not a multiple of 16 bytes are copied by
+//     the CTA itself;
 //  1. a team of T lanes owns node g = (row, i): it forms x, the node's power
 //     of w_k (Montgomery form, from the twiddle table) and its powers, and evaluates
 //     each entry of its columns, sum_l Q[row][entry][l] x^l, with one REDC per
@@ -25,6 +29,7 @@
 //     the elimination of condense_kernel (Algorithm 3).
 #pragma once
 
+#include "bulk.cuh"
 #include "condense.cuh"
 
 // Words of shared memory for the entry slices of a CTA of `threads` lanes.
@@ -125,68 +130,127 @@ __device__ __noinline__ uint2 fused_det(const uint32_t *mine, int bd, int t, Mod
   return make_uint2(Q, den);
 }
 
+// Geometry of one item: its first node g0, the first of the partial-tensor
+// rows it spans and how many, and where those rows start (words into
+// `partial`; they are contiguous).
+struct FusedItem {
+  int64_t g0, row0, src;
+  int nrows, words;
+};
+
+template <int NN>
+__device__ __forceinline__ FusedItem fused_item(const FusedSeg &sg, long long item, int S) {
+  FusedItem f;
+  f.g0 = (item - sg.item0) * S;
+  f.row0 = f.g0 / sg.Mk;
+  const int64_t glast = min(f.g0 + S, sg.G) - 1;
+  f.nrows = (int)(glast / sg.Mk - f.row0 + 1);
+  f.words = f.nrows * NN * NN * sg.Lp;
+  f.src = sg.q_off + f.row0 * NN * NN * (int64_t)sg.Lp;
+  return f;
+}
+
 template <int NN, int T>
 __global__ void __launch_bounds__(128) fused_kernel(const FusedSeg *__restrict__ segs, int nsegs,
                                                     long long nitems,
                                                     const uint32_t *__restrict__ partial,
                                                     uint32_t *__restrict__ detvals,
-                                                    unsigned long long *counter) {
+                                                    unsigned long long *counter, int qwords,
+                                                    int nbuf) {
   constexpr int NN2 = NN * NN;
   extern __shared__ uint4 fused_smem_u4[];
-  __shared__ long long s_item;
-  __shared__ int s_seg;
+  __shared__ long long s_item[2];
+  __shared__ int s_seg[2], s_bulk[2];
+  __shared__ __align__(8) uint64_t s_bar[2];
   const int bd = blockDim.x;
   uint32_t *ent = reinterpret_cast<uint32_t *>(fused_smem_u4);  // [M * NN][bd]
-  uint32_t *qsm = ent + fused_slice_words<NN>(bd);              // [rows][NN2][Lp]
+  uint32_t *qbuf = ent + fused_slice_words<NN>(bd);             // nbuf x [rows][NN2][Lp]
   const int t = (int)(threadIdx.x & (T - 1));
   const int team = threadIdx.x / T;
   __shared__ uint32_t fin_q[128], fin_d[128];
   const int S = bd / T;
 
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const long long it = (long long)atomicAdd(counter, 1ull);
-      int lo = 0;
-      if (it < nitems) {
-        int hi = nsegs - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (segs[mid].item0 <= it) lo = mid; else hi = mid - 1;
-        }
+  // thread 0: take the next item from the counter into slot b and start the
+  // bulk copy of its rows into the slot's buffer (when source, destination
+  // and size are 16-byte multiples; otherwise the CTA copies them itself
+  // later).  With two buffers slot b uses buffer b and the copy overlaps the
+  // previous item; with one (when two do not fit in shared memory) both
+  // slots use buffer 0 and the next item is fetched after the current one.
+  // s_bulk: 0 the CTA copies, 1 a bulk copy is in flight, 2 the test hook
+  // withheld the copy (the wait for it runs out)
+  auto fetch = [&](int b) {
+    const long long it = (long long)atomicAdd(counter, 1ull);
+    int lo = 0, bulk = 0;
+    if (it < nitems) {
+      int hi = nsegs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].item0 <= it) lo = mid; else hi = mid - 1;
       }
-      s_item = it;
-      s_seg = lo;
+      const FusedItem f = fused_item<NN>(segs[lo], it, S);
+      const uint32_t *src = partial + f.src;
+      uint32_t *dst = qbuf + (size_t)(nbuf == 2 ? b : 0) * qwords;
+      bulk = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0 &&
+             (f.words & 3) == 0 && f.words <= qwords;
+      if (bulk && segs[lo].drop_copies) {
+        bulk = 2;
+      } else if (bulk) {
+        pd_fence_proxy_async();
+        pd_mbar_expect_tx(&s_bar[b], (uint32_t)f.words * 4u);
+        pd_bulk_g2s(dst, src, (uint32_t)f.words * 4u, &s_bar[b]);
+      }
     }
-    __syncthreads();
-    const long long item = s_item;
-    const int si = s_seg;
-    __syncthreads();
-    if (item >= nitems) return;
+    s_item[b] = it;
+    s_seg[b] = lo;
+    s_bulk[b] = bulk;
+  };
+
+  if (threadIdx.x == 0) {
+    pd_mbar_init(&s_bar[0], 1);
+    pd_mbar_init(&s_bar[1], 1);
+    pd_mbar_init_fence();
+    fetch(0);
+  }
+  __syncthreads();
+
+  uint32_t phase = 0u;  // bit b: parity of buffer b's barrier phase to wait for
+  for (int cur = 0;; cur ^= 1) {
+    const long long item = s_item[cur];  // written before the last barrier
+    if (item >= nitems) return;          // the same for every thread; nothing in flight
+    const int si = s_seg[cur];
+    const int bulk = s_bulk[cur];
+    // the next item's rows stream in while this one is computed (its slot and
+    // buffer were last read before the barriers of the previous iteration)
+    if (nbuf == 2 && threadIdx.x == 0) fetch(cur ^ 1);
 
     const FusedSeg &sg = segs[si];
+    const FusedItem f = fused_item<NN>(sg, item, S);
+    uint32_t *qsm = qbuf + (size_t)(nbuf == 2 ? cur : 0) * qwords;
+    int late = 0;
+    if (bulk) {
+      late = !pd_mbar_wait_bounded(&s_bar[cur], (phase >> cur) & 1u);
+      phase ^= 1u << cur;
+    } else {  // 0. this item's rows into shared memory by the CTA
+      const uint32_t *src = partial + f.src;
+      for (int w = threadIdx.x; w < f.words; w += bd) qsm[w] = __ldg(src + w);
+    }
+    if (__syncthreads_or(late)) {
+      // a copy did not land in time: report it, let the copy issued above
+      // land (bounded again), and stop this CTA
+      if (threadIdx.x == 0) {
+        if (nbuf == 2 && s_bulk[cur ^ 1] == 1)
+          pd_mbar_wait_bounded(&s_bar[cur ^ 1], (phase >> (cur ^ 1)) & 1u);
+        atomicOr(sg.status, POLYDET_STATUS_TIMEOUT);
+      }
+      return;
+    }
+
     const uint32_t p = sg.md.p, pinv = sg.md.pinv;
     const int logNk = sg.logNk;
     const int64_t Mk = sg.Mk;
     const int Lp = sg.Lp;
-    const int64_t g0 = (item - sg.item0) * S;
-    const int64_t row0 = g0 / Mk;
+    const int64_t g0 = f.g0, row0 = f.row0;
     const int64_t glast = min(g0 + S, sg.G) - 1;
-    const int nrows = (int)(glast / Mk - row0 + 1);
-
-    // 0. this item's Q rows into shared memory (contiguous in global memory)
-    {
-      const uint32_t *src = partial + sg.q_off + row0 * NN2 * (int64_t)Lp;
-      const int words = nrows * NN2 * Lp;
-      if ((Lp & 3) == 0) {
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-        uint4 *d4 = reinterpret_cast<uint4 *>(qsm);
-        for (int w = threadIdx.x; w < (words >> 2); w += bd) d4[w] = __ldg(s4 + w);
-      } else {
-        for (int w = threadIdx.x; w < words; w += bd) qsm[w] = __ldg(src + w);
-      }
-    }
-    __syncthreads();
-
     const int64_t g = g0 + team;
     const bool active = g < sg.G;
     const int64_t gg = active ? g : glast;
@@ -220,41 +284,47 @@ __global__ void __launch_bounds__(128) fused_kernel(const FusedSeg *__restrict__
     if ((int)threadIdx.x < S && g0 + threadIdx.x < sg.G)
       detvals[sg.det_off + g0 + threadIdx.x] =
           finish_det(fin_q[threadIdx.x], fin_d[threadIdx.x], sg.md, sg.rn);
+    if (nbuf == 1) {  // the one buffer was last read before the barrier above
+      if (threadIdx.x == 0) fetch(cur ^ 1);
+      __syncthreads();
+    }
     (void)active;
   }
 }
 
-// Dynamic shared memory of a fused CTA: entry slices + `qwords` of Q rows.
+// Dynamic shared memory of a fused CTA: entry slices + `nbuf` buffers of
+// `qwords` words of Q rows (qwords a multiple of 4: each starts on 16 bytes).
 template <int NN>
-constexpr size_t fused_smem(int threads, size_t qwords) {
-  return (fused_slice_words<NN>(threads) + qwords) * sizeof(uint32_t);
+constexpr size_t fused_smem(int threads, size_t qwords, int nbuf) {
+  return (fused_slice_words<NN>(threads) + (size_t)nbuf * qwords) * sizeof(uint32_t);
 }
 
 template <int NN, int HI>
 static int fused_dispatch(int n, const FusedSeg *segs, int nsegs, int64_t nitems,
                           const uint32_t *partial, uint32_t *detvals, unsigned long long *counter,
-                          int threads, int blocks, size_t qwords, cudaStream_t st) {
+                          int threads, int blocks, size_t qwords, int nbuf, cudaStream_t st) {
   if (n == NN) {
-    fused_kernel<NN, TeamFor<NN>::value><<<blocks, threads, fused_smem<NN>(threads, qwords), st>>>(
-        segs, nsegs, (long long)nitems, partial, detvals, counter);
+    fused_kernel<NN, TeamFor<NN>::value><<<blocks, threads, fused_smem<NN>(threads, qwords, nbuf), st>>>(
+        segs, nsegs, (long long)nitems, partial, detvals, counter, (int)qwords, nbuf);
     PD_CUDA(cudaGetLastError());
     return POLYDET_OK;
   }
   if constexpr (NN < HI) {
     return fused_dispatch<NN + 1, HI>(n, segs, nsegs, nitems, partial, detvals, counter, threads,
-                                      blocks, qwords, st);
+                                      blocks, qwords, nbuf, st);
   }
   return POLYDET_EINVAL;
 }
 
-// Occupancy of order n at `threads` lanes and `qwords` words of Q rows; also
+// Occupancy of order n at `threads` lanes and `nbuf` buffers of `qwords`
+// words of Q rows; also
 // raises the kernel's dynamic shared-memory limit (call before any graph
 // capture: the batch plan and polydet_batch_set_launch do).  Reports 0 when
 // the CTA does not fit.
 template <int NN, int HI>
-static int fused_occ_dispatch(int n, int threads, size_t qwords, int *bps) {
+static int fused_occ_dispatch(int n, int threads, size_t qwords, int nbuf, int *bps) {
   if (n == NN) {
-    const size_t smem = fused_smem<NN>(threads, qwords);
+    const size_t smem = fused_smem<NN>(threads, qwords, nbuf);
     if (smem > 220 * 1024) {
       *bps = 0;
       return POLYDET_OK;
@@ -265,6 +335,6 @@ static int fused_occ_dispatch(int n, int threads, size_t qwords, int *bps) {
                                                           threads, smem));
     return POLYDET_OK;
   }
-  if constexpr (NN < HI) return fused_occ_dispatch<NN + 1, HI>(n, threads, qwords, bps);
+  if constexpr (NN < HI) return fused_occ_dispatch<NN + 1, HI>(n, threads, qwords, nbuf, bps);
   return POLYDET_EINVAL;
 }

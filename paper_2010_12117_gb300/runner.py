@@ -29,8 +29,11 @@ class StageTimer:
         self.events: Dict[str, list] = defaultdict(list)
         self.work: Dict[str, float] = defaultdict(float)
         self.launches: Dict[str, int] = defaultdict(int)
+        self.tagged: Dict[tuple, list] = defaultdict(list)  # (name, tag) -> event pairs
+        self.tag_work: Dict[tuple, float] = defaultdict(float)
 
-    def run(self, name: str, stream: torch.cuda.Stream, fn, work: float = 0.0, launches: int = 1):
+    def run(self, name: str, stream: torch.cuda.Stream, fn, work: float = 0.0, launches: int = 1,
+            tag=None):
         s = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
         s.record(stream)
@@ -39,9 +42,17 @@ class StageTimer:
         self.events[name].append((s, e))
         self.work[name] += work
         self.launches[name] += launches
+        if tag is not None:
+            self.tagged[(name, tag)].append((s, e))
+            self.tag_work[(name, tag)] += work
 
     def ms(self) -> Dict[str, float]:
         return {k: sum(s.elapsed_time(e) for s, e in v) for k, v in self.events.items()}
+
+    def tag_ms(self, name: str) -> Dict:
+        """Per tag of stage ``name``: (milliseconds, work)."""
+        return {t: (sum(s.elapsed_time(e) for s, e in v), self.tag_work[(nm, t)])
+                for (nm, t), v in self.tagged.items() if nm == name}
 
 
 def condense_updates(n: int) -> int:
@@ -129,7 +140,7 @@ class PlainRunner:
                     if timer is None:
                         fn()
                     else:
-                        timer.run(name, stream, fn, work, nl)
+                        timer.run(name, stream, fn, work, nl, tag=pm.n)
             lb = self.limbs[self.limb_off[i]:self.limb_off[i + 1]]
             fn = lambda: pl.crt(res, lb, stream)  # noqa: E731
             if timer is None:

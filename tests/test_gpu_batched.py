@@ -229,3 +229,54 @@ def test_one_by_one_and_constant_jobs_in_both_modes():
         assert got[0] == mats[0].coeffs[0, 0].tolist()
         for pm, g in zip(mats[1:], got[1:]):
             assert g == plain(pm), (mode, pm.n, pm.degs)
+
+
+def test_withheld_bulk_copies_time_out_and_are_reported():
+    """Failure detection without a fault: with the test hook on, the fused
+    kernel's bounded wait for its staged rows runs out (about a second), the
+    CTA sets the TIMEOUT bit of the status word and ends; with the hook off
+    again the same batch gives the plain form's integers."""
+    import time
+    from paper_2010_12117_gb300.binding import BATCH_FUSED
+    from paper_2010_12117_gb300.runner import BatchedRunner
+    rng = np.random.default_rng(77)
+    # last variable of degree 2 (L = 3, rows of n^2 x 4 words): every item's
+    # rows start and end on 16 bytes, so every item takes the bulk copy
+    mats = [synth.random_matrix(rng, n, (2, 3), 0.8, -50, 50) for n in (4, 6, 8)]
+    want = [plain(pm) for pm in mats]
+    st = torch.cuda.Stream()
+    r = BatchedRunner(mats, tune=False, stream=st)
+    r.set_modes(BATCH_FUSED)
+    r.upload(st)
+    r.batch.test_drop_copies(True)
+    t0 = time.perf_counter()
+    r.compute(st)
+    st.synchronize()
+    dt = time.perf_counter() - t0
+    status = r.batch.sync_status(st)  # reads and clears every job's word
+    assert status & 0x2, status
+    assert 0.5 < dt < 60, dt
+    r.batch.test_drop_copies(False)
+    r.compute(st)
+    r.download(st)
+    st.synchronize()
+    r.check_status(st)
+    assert r.results() == want
+    r.close()
+
+
+def test_fused_staging_with_one_buffer_and_unaligned_rows():
+    """Jobs whose last variable has degree 0 (one node per row, rows of n^2
+    words): at n = 12, 13 two staging buffers do not fit in shared memory and
+    the fused kernel runs with one; rows of odd n^2 words start off 16 bytes
+    and are copied by the CTA, the others by bulk copies.  Same integers as
+    the plain form."""
+    from paper_2010_12117_gb300.binding import BATCH_FUSED
+    rng = np.random.default_rng(91)
+    mats = [synth.random_matrix(rng, 13, (2, 0), 0.7, -40, 40),
+            synth.random_matrix(rng, 12, (0, 3), 0.7, -40, 40),
+            synth.random_matrix(rng, 11, (1, 0), 0.9, -40, 40),
+            synth.random_matrix(rng, 5, (0, 0, 2), 1.0, -40, 40)]
+    got = batched_results(mats, modes=BATCH_FUSED)
+    for pm, g in zip(mats, got):
+        assert g == plain(pm), (pm.n, pm.degs)
