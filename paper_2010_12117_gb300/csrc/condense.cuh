@@ -1,9 +1,12 @@
 // Determinant mod p of one n x n matrix per grid node (Sec. 3.2, Algorithm 3).
 //
 // A team of T consecutive lanes owns one matrix: lane t holds the columns
-// j = t, t + T, t + 2T, ... entirely in registers (one lane for n <= 15,
-// up to 16 lanes at n = 32; the per-order T and the CTAs per SM the kernel is
-// compiled for are the table of teams.cuh).  Every index into the register
+// j = t - s, t - s + T, t - s + 2T, ... entirely in registers (one lane for
+// n <= 15, up to 16 lanes at n = 32; the per-order T and the CTAs per SM the
+// kernel is compiled for are the table of teams.cuh).  The s = T ceil(n/T) - n
+// padding slots (j < 0) sit in the first block of T columns, which drops out
+// of the elimination after its first steps; in the last block they would be
+// computed and discarded at almost every step.  Every index into the register
 // array is a compile-time constant after unrolling, and there are no
 // barriers: the team talks through warp shuffles.
 //
@@ -30,13 +33,28 @@
 
 #define PD_FULL 0xffffffffu
 
-// Whether lane t's m-th column j = t + T m lies strictly between lo and NN.
-// After unrolling m and lo are constants, so every part that does not depend
-// on t folds away: columns wholly inside or outside the range cost nothing,
-// only the one column block that straddles `lo` keeps a run-time test.
+// Column slots of a team of T lanes: M per lane, the first S of block 0
+// padding (no column).
+template <int NN, int T>
+struct ColLayout {
+  static constexpr int M = (NN + T - 1) / T;
+  static constexpr int S = T * M - NN;
+};
+
+// The column held in slot m of lane t (negative: padding).
+template <int NN, int T>
+PD_D int col_of(int t, int m) {
+  return T * m + t - ColLayout<NN, T>::S;
+}
+
+// Whether lane t's m-th column j = col_of(t, m) lies strictly between lo and
+// NN.  After unrolling m and lo are constants, so every part that does not
+// depend on t folds away: columns wholly inside or outside the range cost
+// nothing, only a column block that straddles `lo` keeps a run-time test.
 template <int NN, int T>
 PD_D bool col_in(int t, int m, int lo) {
-  const int jmin = T * m, jmax = T * m + T - 1;
+  constexpr int S = ColLayout<NN, T>::S;
+  const int jmin = T * m - S, jmax = T * m + T - 1 - S;
   if (jmin > lo && jmax < NN) return true;
   if (jmax <= lo || jmin >= NN) return false;
   const int j = jmin + t;
@@ -58,8 +76,8 @@ struct ElimStep {
   static constexpr int M = (NN + T - 1) / T;
   static PD_D void run(uint32_t (&a)[M][NN], int t, uint32_t p, uint32_t pinv, uint32_t &Q,
                        uint32_t &den) {
-    constexpr int owner = c % T;
-    constexpr int mc = c / T;
+    constexpr int owner = (c + ColLayout<NN, T>::S) % T;
+    constexpr int mc = (c + ColLayout<NN, T>::S) / T;
     uint32_t piv = (T == 1) ? a[mc][c] : __shfl_sync(PD_FULL, a[mc][c], owner, T);
     if (c < NN - 1) {
       if (__any_sync(PD_FULL, piv == 0u)) {
@@ -118,8 +136,8 @@ struct FastStep {
   static constexpr int M = (NN + T - 1) / T;
   static PD_D void run(uint32_t (&a)[M][NN], int t, uint32_t p, uint32_t pinv, uint32_t &Q,
                        uint32_t &den, bool &zero) {
-    constexpr int owner = c % T;
-    constexpr int mc = c / T;
+    constexpr int owner = (c + ColLayout<NN, T>::S) % T;
+    constexpr int mc = (c + ColLayout<NN, T>::S) / T;
     const uint32_t piv = (T == 1) ? a[mc][c] : __shfl_sync(PD_FULL, a[mc][c], owner, T);
     zero |= (piv == 0u);
     if (c < NN - 1) {
@@ -130,14 +148,16 @@ struct FastStep {
         const uint32_t fi = (T == 1) ? a[mc][i] : __shfl_sync(PD_FULL, a[mc][i], owner, T);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          // blocks of columns wholly right of c update unconditionally; the
-          // one block that straddles c keeps its old values by a select, so
-          // the whole elimination stays one branch-free block of code
-          if (T * m > c && T * m + T - 1 < NN) {
+          // blocks of columns wholly right of c update unconditionally; a
+          // block that straddles c (or holds padding) keeps its old values
+          // by a select, so the whole elimination stays one branch-free
+          // block of code
+          constexpr int S = ColLayout<NN, T>::S;
+          if (T * m - S > c && T * m + T - 1 - S < NN) {
             a[m][i] = mfms(piv, a[m][i], fi, a[m][c], p, pinv);
-          } else if (!(T * m + T - 1 <= c || T * m >= NN)) {
+          } else if (!(T * m + T - 1 - S <= c || T * m - S >= NN)) {
             const uint32_t v = mfms(piv, a[m][i], fi, a[m][c], p, pinv);
-            const int j = T * m + t;
+            const int j = col_of<NN, T>(t, m);
             a[m][i] = (j > c && j < NN) ? v : a[m][i];
           }
         }
@@ -166,9 +186,9 @@ __device__ __noinline__ uint2 elim_search(const uint32_t *base, int64_t stride, 
   uint32_t a[M][NN];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const int j = t + T * m;
+    const int j = col_of<NN, T>(t, m);
 #pragma unroll
-    for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? base[(int64_t)(i * NN + j) * stride] : 0u;
+    for (int i = 0; i < NN; ++i) a[m][i] = (j >= 0) ? base[(int64_t)(i * NN + j) * stride] : 0u;
   }
   uint32_t Q = md.r1, den = md.r1;
   ElimStep<NN, T, 0>::run(a, t, md.p, md.pinv, Q, den);
@@ -198,9 +218,9 @@ __global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__r
   uint32_t a[M][NN];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const int j = t + T * m;
+    const int j = col_of<NN, T>(t, m);
 #pragma unroll
-    for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? __ldg(base + (int64_t)(i * NN + j) * Gs) : 0u;
+    for (int i = 0; i < NN; ++i) a[m][i] = (j >= 0) ? __ldg(base + (int64_t)(i * NN + j) * Gs) : 0u;
   }
 
   uint32_t Q = md.r1, den = md.r1;

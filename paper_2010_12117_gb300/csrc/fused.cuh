@@ -45,8 +45,8 @@ __device__ __forceinline__ void fused_eval_entries(const uint32_t *qrow, int t, 
   constexpr int M = (NN + T - 1) / T;
 #pragma unroll 1
   for (int m = 0; m < M; ++m) {
-    const int j = t + T * m;
-    if (j >= NN) break;
+    const int j = col_of<NN, T>(t, m);
+    if (j < 0) continue;  // padding slot (condense.cuh): its registers are zeroed on load
 #pragma unroll 2
     for (int i = 0; i < NN; ++i) {
       const uint32_t *q = qrow + (i * NN + j) * Lp;
@@ -99,9 +99,9 @@ __device__ __noinline__ uint2 fused_det_search(const uint32_t *mine, int bd, int
   uint32_t a[M][NN];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const int j = t + T * m;
+    const int j = col_of<NN, T>(t, m);
 #pragma unroll
-    for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? mine[(m * NN + i) * bd] : 0u;
+    for (int i = 0; i < NN; ++i) a[m][i] = (j >= 0) ? mine[(m * NN + i) * bd] : 0u;
   }
   uint32_t Q = md.r1, den = md.r1;
   ElimStep<NN, T, 0>::run(a, t, md.p, md.pinv, Q, den);
@@ -118,9 +118,9 @@ __device__ __noinline__ uint2 fused_det(const uint32_t *mine, int bd, int t, Mod
   uint32_t a[M][NN];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const int j = t + T * m;
+    const int j = col_of<NN, T>(t, m);
 #pragma unroll
-    for (int i = 0; i < NN; ++i) a[m][i] = (j < NN) ? mine[(m * NN + i) * bd] : 0u;
+    for (int i = 0; i < NN; ++i) a[m][i] = (j >= 0) ? mine[(m * NN + i) * bd] : 0u;
   }
   uint32_t Q = md.r1, den = md.r1;
   bool zero = false;
