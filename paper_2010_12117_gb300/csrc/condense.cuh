@@ -126,7 +126,8 @@ struct ElimStep<NN, T, NN> {
 };
 
 // The same elimination without the pivot search: no warp vote per step, so
-// the steps overlap freely (the vote is a convergence point on every step).
+// the steps overlap freely (the vote is a convergence point on every step),
+// and without the per-column range test (see the update below).
 // A zero pivot is only recorded in `zero`; the caller then redoes the whole
 // matrix with ElimStep.  For matrices with nonzero leading minors - almost
 // every node of a random polynomial matrix mod a 31-bit prime - the result
@@ -148,18 +149,13 @@ struct FastStep {
         const uint32_t fi = (T == 1) ? a[mc][i] : __shfl_sync(PD_FULL, a[mc][i], owner, T);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          // blocks of columns wholly right of c update unconditionally; a
-          // block that straddles c (or holds padding) keeps its old values
-          // by a select, so the whole elimination stays one branch-free
-          // block of code
+          // every block that still holds a column j > c updates all its
+          // lanes, with no select: in a block that straddles c, columns
+          // j < c and padding slots are never read again, and column c
+          // itself becomes a_cc a_ic - a_ic a_cc = 0 after its entries were
+          // broadcast; blocks wholly left of c drop out at compile time
           constexpr int S = ColLayout<NN, T>::S;
-          if (T * m - S > c && T * m + T - 1 - S < NN) {
-            a[m][i] = mfms(piv, a[m][i], fi, a[m][c], p, pinv);
-          } else if (!(T * m + T - 1 - S <= c || T * m - S >= NN)) {
-            const uint32_t v = mfms(piv, a[m][i], fi, a[m][c], p, pinv);
-            const int j = col_of<NN, T>(t, m);
-            a[m][i] = (j > c && j < NN) ? v : a[m][i];
-          }
+          if (T * m + T - 1 - S > c) a[m][i] = mfms(piv, a[m][i], fi, a[m][c], p, pinv);
         }
       }
       Q = mmul(Q, piv, p, pinv);
