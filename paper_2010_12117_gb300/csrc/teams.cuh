@@ -8,7 +8,7 @@
 // chosen per order from a sweep of both on GB300 with random 31-bit matrices
 // (2^18 nodes): one lane while the whole matrix fits in registers, then the
 // pair that kept the elimination the least latency-bound.
-constexpr int kTeam[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4,
-                                          2, 2, 4, 4, 4, 4, 4, 8, 8, 8, 4, 4, 8, 8, 8, 16};
-constexpr int kMinBlocks[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
-                                               3, 1, 4, 3, 3, 3, 3, 4, 3, 3, 1, 1, 3, 3, 3, 4};
+constexpr int kTeam[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 2,
+                                          2, 4, 4, 4, 4, 4, 4, 8, 8, 8, 4, 4, 8, 8, 8, 16};
+constexpr int kMinBlocks[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 2,
+                                               3, 4, 4, 4, 3, 3, 3, 4, 3, 3, 1, 1, 3, 3, 3, 4};
