@@ -22,14 +22,19 @@ def main(argv=None) -> int:
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--mode", choices=("default", "fused", "materialized"), default="default")
     ap.add_argument("--chunk-words", type=int, default=0, help="materialized chunk budget (0: default)")
-    ap.add_argument("--stage", choices=("det", "eval", "crt"), default="det",
+    ap.add_argument("--stage", choices=("det", "eval", "crt", "batched"), default="det",
                     help="det: the whole job in both forms; eval: the evaluation of the 12x12 "
-                         "trivariate workload alone; crt: the CRT of 2^24 coefficients alone")
+                         "trivariate workload alone; crt: the CRT of 2^24 coefficients alone; "
+                         "batched: two steps of the 256-matrix batched workload (seed 0, the "
+                         "autotuner's cached choices, CUDA graphs), the second between "
+                         "cudaProfilerStart and cudaProfilerStop")
     ap.add_argument("--primes", type=int, default=5, help="primes for --stage eval / crt")
     ap.add_argument("--full-grid", action="store_true", help="--stage eval on the power-of-two grid")
     args = ap.parse_args(argv)
 
     import torch
+    if args.stage == "batched":
+        return _batched()
     if args.stage != "det":
         return _stage(args)
     from . import synth
@@ -67,6 +72,27 @@ def main(argv=None) -> int:
         print("MISMATCH between the plain and the batched form", sizes)
         return 1
     print("ok", sizes)
+    return 0
+
+
+def _batched() -> int:
+    """One warm step and one profiled step of the batched workload."""
+    import torch
+    from . import synth
+    from .runner import BatchedRunner
+    st = torch.cuda.Stream()
+    r = BatchedRunner(synth.batched(0, 256), tune="cache", stream=st)
+    r.upload(st)
+    r.capture(st)
+    r.compute(st)
+    st.synchronize()
+    torch.cuda.profiler.start()
+    r.compute(st)
+    st.synchronize()
+    torch.cuda.profiler.stop()
+    r.check_status(st)
+    print("ok batched step:", r.modp_dets(), "determinants mod p, modes", r.tuning or "default")
+    r.close()
     return 0
 
 

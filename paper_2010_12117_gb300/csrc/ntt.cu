@@ -44,6 +44,10 @@ struct TxArgs {
   // node order of the output rows (forward passes): row k holds the value at
   // w^node_exp(k, N, olp); 0 or 1: natural order
   int olp;
+  // register-direct kernel only: 0 = one grid row per item (blockIdx.y);
+  // otherwise the number of items, and the grid's x axis runs over
+  // (item, column) pairs, so that short rows still fill whole CTAs
+  int flat_items;
 };
 
 __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
@@ -188,9 +192,18 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
   const ModP md = a.mod[q];
   const uint32_t p = md.p, pinv = md.pinv;
   const int64_t ncols = a.A * a.B;
-  const int64_t col0 = (int64_t)blockIdx.x * blockDim.x * CPT + threadIdx.x;
-  if (col0 >= ncols) return;
-  const int64_t in_base = (int64_t)blockIdx.z * a.in_prime_stride + (int64_t)blockIdx.y * a.in_item_stride;
+  int64_t item, col0;
+  if (a.flat_items) {  // CPT == 1; items * ncols < 2^31 (launch_pass)
+    const int gc = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (gc >= a.flat_items * (int)ncols) return;
+    item = gc / (int)ncols;
+    col0 = gc - item * ncols;
+  } else {
+    item = blockIdx.y;
+    col0 = (int64_t)blockIdx.x * blockDim.x * CPT + threadIdx.x;
+    if (col0 >= ncols) return;
+  }
+  const int64_t in_base = (int64_t)blockIdx.z * a.in_prime_stride + item * a.in_item_stride;
   const int N = a.N;
   const int J = N / LP;
   int64_t ostride;
@@ -213,10 +226,10 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
     }
     int64_t obase;
     if (a.il_L)
-      obase = (int64_t)blockIdx.z * a.out_prime_stride + ((bb / a.il_L) * a.il_n2 + blockIdx.y) * a.il_Lp +
+      obase = (int64_t)blockIdx.z * a.out_prime_stride + ((bb / a.il_L) * a.il_n2 + item) * a.il_Lp +
               bb % a.il_L;
     else
-      obase = (int64_t)blockIdx.z * a.out_prime_stride + (int64_t)blockIdx.y * a.out_item_stride +
+      obase = (int64_t)blockIdx.z * a.out_prime_stride + item * a.out_item_stride +
               aa * a.Lout * ostride + bb;
     op[k] = ok ? a.out + obase : nullptr;
   }
@@ -303,6 +316,7 @@ static int ilog2(int64_t x) {
 template <int CPT>
 static int launch_direct(const TxArgs &a, int64_t ncols, int items, int nprimes, cudaStream_t st) {
   dim3 grid((unsigned)((ncols + 256 * CPT - 1) / (256 * CPT)), (unsigned)items, (unsigned)nprimes);
+  if (a.flat_items) grid = dim3((unsigned)((ncols * items + 255) / 256), 1u, (unsigned)nprimes);
   switch (a.Lin) {
     case 1: coltx_direct_kernel<1, CPT><<<grid, 256, 0, st>>>(a); break;
     case 2: coltx_direct_kernel<2, CPT><<<grid, 256, 0, st>>>(a); break;
@@ -325,6 +339,10 @@ static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
     // columns per thread: more share each coset's twiddles, fewer leave
     // fewer idle lanes in the last CTA of a row of B columns
     const int cpt = ncols >= 8192 ? 4 : (ncols >= 2048 ? 2 : 1);
+    // short rows (one column per thread): one grid axis over (item, column)
+    // pairs, so that rows shorter than a CTA, or a row's last CTA, leave no
+    // threads idle
+    a.flat_items = (cpt == 1 && ncols * items < ((int64_t)1 << 31) - 256) ? items : 0;
     switch (cpt) {
       case 4: return launch_direct<4>(a, ncols, items, nprimes, st);
       case 2: return launch_direct<2>(a, ncols, items, nprimes, st);
