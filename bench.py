@@ -335,6 +335,33 @@ def served_leg(args, mats, batched_value, st):
         srv = Server(p, mem_budget=40e9, slots=3, wave_seconds=0.02)
         rep = srv.run(stream, keep_results=False)
         out[name] = rep.summary()
+    # capacity: the same jobs all waiting at t = 0 (MLP admission), against the
+    # plain per-matrix form over the same jobs (one pass, CUDA events)
+    import torch
+    from paper_2010_12117_gb300.runner import PlainRunner
+    backlog = [synth.Arrival(0.0, a.job) for a in stream]
+    rep = Server(pr, mem_budget=40e9, slots=3, wave_seconds=0.02).run(backlog, keep_results=False)
+    out["saturated"] = rep.summary()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    plain = PlainRunner([a.job for a in stream])  # plans, buffers, upload, run, download
+    plain.upload(st)
+    plain.compute(st)
+    plain.download(st)
+    st.synchronize()
+    wall = time.perf_counter() - w0
+    s_ev = torch.cuda.Event(enable_timing=True)
+    e_ev = torch.cuda.Event(enable_timing=True)
+    s_ev.record(st)
+    plain.compute(st)
+    e_ev.record(st)
+    e_ev.synchronize()
+    ms = s_ev.elapsed_time(e_ev)
+    plain.close()
+    out["plain_same_jobs"] = {"wall_s": wall, "exact_dets_per_s": len(stream) / wall,
+                              "device_ms": ms, "device_exact_dets_per_s": len(stream) / (ms * 1e-3),
+                              "note": "wall: plans, buffers, upload, one pass, download (like the "
+                                      "server's waves); device: one pass with inputs resident"}
     return out
 
 
