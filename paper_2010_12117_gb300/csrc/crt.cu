@@ -97,18 +97,19 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
   uint32_t xn[PT];
   int64_t c0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
   if (c0 < C) {
-    const int64_t c = c0 + lane < C ? c0 + lane : C - 1;
+    const uint32_t *rp = res + (c0 + lane < C ? c0 + lane : C - 1);
 #pragma unroll
-    for (int i = 0; i < PT; ++i) xn[i] = __ldg(res + (int64_t)i * C + c);
+    for (int i = 0; i < PT; ++i, rp += C) xn[i] = __ldg(rp);
   }
   for (; c0 < C; c0 += stride) {
     uint32_t x[PT], al[PT];
 #pragma unroll
     for (int i = 0; i < PT; ++i) x[i] = xn[i];
     if (c0 + stride < C) {
-      const int64_t c = c0 + stride + lane < C ? c0 + stride + lane : C - 1;  // the warp stays whole
+      // the warp stays whole: lanes past the end read the last coefficient
+      const uint32_t *rp = res + (c0 + stride + lane < C ? c0 + stride + lane : C - 1);
 #pragma unroll
-      for (int i = 0; i < PT; ++i) xn[i] = __ldg(res + (int64_t)i * C + c);
+      for (int i = 0; i < PT; ++i, rp += C) xn[i] = __ldg(rp);
     }
     // Garner digits (Sec. 3.4): alpha_i = x_i c_i - sum_{j<i} alpha_j m_j c_i
     // mod p_i as one dot product; two 62-bit products (each below 2^31 p_i)
@@ -160,9 +161,13 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
     for (int w = 0; w < PT; ++w)
       if (w < W) sw[lane * W + w] = X[w];
     __syncwarp();
-    const int64_t nw = (C - c0 < 32 ? C - c0 : 32) * W;  // words of this warp's coefficients
+    const int nw = (C - c0 < 32 ? (int)(C - c0) : 32) * W;  // words of this warp's coefficients
     uint32_t *o = limbs + c0 * W;
-    for (int f = lane; f < nw; f += 32) o[f] = sw[f];
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {  // W <= PT rounds of 32 consecutive words
+      const int f = lane + 32 * k;
+      if (k < W && f < nw) o[f] = sw[f];
+    }
     __syncwarp();
   }
 }
