@@ -335,10 +335,13 @@ static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
   int64_t ncols = a.A * a.B;
   // short forward transforms over many columns: the register-direct kernel
   const int lp_in = a.Lin <= 1 ? 1 : a.Lin <= 2 ? 2 : a.Lin <= 4 ? 4 : 8;
-  if (!a.inverse && a.Lin <= 8 && a.B >= 8 && (a.olp <= 1 || a.olp == lp_in)) {
+  // rows of fewer than 8 columns (a job's first pass: B = 1) only with the
+  // flattened grid below, and not into the interleaved partial layout
+  const bool rows_ok = a.B >= 8 || (!a.il_L && ncols * items < ((int64_t)1 << 31) - 256);
+  if (!a.inverse && a.Lin <= 8 && rows_ok && (a.olp <= 1 || a.olp == lp_in)) {
     // columns per thread: more share each coset's twiddles, fewer leave
     // fewer idle lanes in the last CTA of a row of B columns
-    const int cpt = ncols >= 8192 ? 4 : (ncols >= 2048 ? 2 : 1);
+    const int cpt = a.B < 8 ? 1 : (ncols >= 8192 ? 4 : (ncols >= 2048 ? 2 : 1));
     // short rows (one column per thread): one grid axis over (item, column)
     // pairs, so that rows shorter than a CTA, or a row's last CTA, leave no
     // threads idle
