@@ -46,8 +46,9 @@ struct TxArgs {
   int olp;
   // register-direct kernel only: 0 = one grid row per item (blockIdx.y);
   // otherwise the number of items, and the grid's x axis runs over
-  // (item, column) pairs, so that short rows still fill whole CTAs
-  int flat_items;
+  // (item, column, coset group) triples, so that short rows still fill whole
+  // CTAs; each column's cosets are cut into flat_groups consecutive groups
+  int flat_items, flat_groups;
 };
 
 __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
@@ -193,11 +194,14 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
   const uint32_t p = md.p, pinv = md.pinv;
   const int64_t ncols = a.A * a.B;
   int64_t item, col0;
-  if (a.flat_items) {  // CPT == 1; items * ncols < 2^31 (launch_pass)
+  int grp = 0;
+  if (a.flat_items) {  // CPT == 1; items * ncols * groups < 2^31 (launch_pass)
     const int gc = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (gc >= a.flat_items * (int)ncols) return;
-    item = gc / (int)ncols;
-    col0 = gc - item * ncols;
+    if (gc >= a.flat_items * (int)ncols * a.flat_groups) return;
+    const int pair = gc / a.flat_groups;
+    grp = gc - pair * a.flat_groups;
+    item = pair / (int)ncols;
+    col0 = pair - item * ncols;
   } else {
     item = blockIdx.y;
     col0 = (int64_t)blockIdx.x * blockDim.x * CPT + threadIdx.x;
@@ -254,7 +258,16 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
     toff[t] = (int64_t)(coset_rows ? t : J * t) * ostride;
   }
   const int64_t jstep = (int64_t)(coset_rows ? LP : 1) * ostride;  // next coset's first row
-  for (int j = 0; j < Jc; ++j) {
+  int jlo = 0, jhi = Jc;  // this thread's cosets
+  if (a.flat_items && a.flat_groups > 1) {
+    const int per = (Jc + a.flat_groups - 1) / a.flat_groups;
+    jlo = min(Jc, grp * per);
+    jhi = min(Jc, jlo + per);
+#pragma unroll
+    for (int k = 0; k < CPT; ++k)
+      if (op[k]) op[k] += jlo * jstep;
+  }
+  for (int j = jlo; j < jhi; ++j) {
     uint32_t w[LIN];
     w[0] = md.r1;
 #pragma unroll
@@ -316,7 +329,8 @@ static int ilog2(int64_t x) {
 template <int CPT>
 static int launch_direct(const TxArgs &a, int64_t ncols, int items, int nprimes, cudaStream_t st) {
   dim3 grid((unsigned)((ncols + 256 * CPT - 1) / (256 * CPT)), (unsigned)items, (unsigned)nprimes);
-  if (a.flat_items) grid = dim3((unsigned)((ncols * items + 255) / 256), 1u, (unsigned)nprimes);
+  if (a.flat_items)
+    grid = dim3((unsigned)((ncols * items * a.flat_groups + 255) / 256), 1u, (unsigned)nprimes);
   switch (a.Lin) {
     case 1: coltx_direct_kernel<1, CPT><<<grid, 256, 0, st>>>(a); break;
     case 2: coltx_direct_kernel<2, CPT><<<grid, 256, 0, st>>>(a); break;
@@ -346,6 +360,18 @@ static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
     // pairs, so that rows shorter than a CTA, or a row's last CTA, leave no
     // threads idle
     a.flat_items = (cpt == 1 && ncols * items < ((int64_t)1 << 31) - 256) ? items : 0;
+    // few columns in all (a job's first pass): cut each column's cosets into
+    // groups until the grid holds about 152 x 1024 threads
+    a.flat_groups = 1;
+    if (a.flat_items) {
+      const int J = a.N / lp_in;
+      const int Jc = (a.olp > 1) ? (a.Lout + lp_in - 1) / lp_in : J;
+      const int64_t base = ncols * items * nprimes;
+      int64_t g = (152 * 1024 + base - 1) / base;
+      g = std::min<int64_t>(g, Jc);
+      while (g > 1 && ncols * items * g >= ((int64_t)1 << 31) - 256) --g;
+      a.flat_groups = (int)std::max<int64_t>(1, g);
+    }
     switch (cpt) {
       case 4: return launch_direct<4>(a, ncols, items, nprimes, st);
       case 2: return launch_direct<2>(a, ncols, items, nprimes, st);
