@@ -14,7 +14,10 @@ factor.  Here the same idea is carried to the batched GPU form in two layers:
   measured timings and footprints, with forward, backward and Adam in the
   library's CUDA kernels.  Inputs: n, k, max and mean degree, density,
   coefficient bits, and the logs of the analytic time and memory; outputs:
-  log time and log memory (standardised).  The analytic bound judges it:
+  log(measured / analytic) for time and memory (standardised), a correction
+  to the bound, so that a network with a constant output reproduces the
+  calibrated bound and training adds what the shape tells beyond it.  The
+  analytic bound judges it:
   a prediction below the bound is raised to it, one more than ``max_ratio``
   times the larger of the bound and the smallest measured value falls back
   to the bound times the calibrated median ratio, and an untrained predictor
@@ -176,11 +179,12 @@ class Predictor:
         """X [B][8] features, Y [B][2] measured (seconds, bytes), bounds [B][2]
         analytic (seconds, bytes).  Full-batch Adam on the GPU kernels."""
         logy = np.log(np.maximum(Y, 1e-12)).astype(np.float64)
-        self.mu = logy.mean(0).astype(np.float32)
-        self.sd = np.maximum(logy.std(0), 1e-3).astype(np.float32)
-        self.ratio = np.exp(np.median(logy - np.log(bounds), axis=0))
+        logr = logy - np.log(np.maximum(bounds, 1e-12))  # the correction to the bound
+        self.mu = logr.mean(0).astype(np.float32)
+        self.sd = np.maximum(logr.std(0), 1e-3).astype(np.float32)
+        self.ratio = np.exp(np.median(logr, axis=0))
         self.floor = np.min(Y, axis=0).astype(np.float64)
-        T = ((logy - self.mu) / self.sd).astype(np.float32)
+        T = ((logr - self.mu) / self.sd).astype(np.float32)
         B = len(X)
         x = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(self.dev)
         t = torch.from_numpy(np.ascontiguousarray(T)).to(self.dev)
@@ -202,13 +206,14 @@ class Predictor:
         return hist
 
     # -- inference -----------------------------------------------------------
-    def raw(self, X: np.ndarray) -> np.ndarray:
-        """MLP outputs mapped back to (seconds, bytes), unjudged."""
+    def raw(self, X: np.ndarray, bounds: np.ndarray) -> np.ndarray:
+        """MLP outputs mapped back to (seconds, bytes) for jobs with analytic
+        bounds ``bounds`` [len][2], unjudged."""
         x = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(self.dev)
         y = torch.empty(len(X), 2, device=self.dev)
         binding.mlp_forward(self.params, x, y, None)
         out = y.cpu().numpy().astype(np.float64) * self.sd + self.mu
-        return np.exp(out)
+        return np.asarray(bounds, dtype=np.float64) * np.exp(out)
 
     def predict(self, shapes: Sequence[Shape]) -> np.ndarray:
         """Judged predictions [len][2] = (seconds, bytes)."""
@@ -216,7 +221,7 @@ class Predictor:
         if not self.trained or len(shapes) == 0:
             return bounds * self.ratio
         X = np.stack([features(s) for s in shapes])
-        pred = self.raw(X)
+        pred = self.raw(X, bounds)
         pred = np.maximum(pred, bounds)
         # implausibly large: more than max_ratio times the bound, or than the
         # smallest footprint / time ever measured when the bound is below it
