@@ -2,7 +2,7 @@
 //
 // A team of T consecutive lanes owns one matrix: lane t holds the columns
 // j = t - s, t - s + T, t - s + 2T, ... entirely in registers (one lane for
-// n <= 15, up to 16 lanes at n = 32; the per-order T and the CTAs per SM the
+// most n <= 15, up to 16 lanes at n = 32; the per-order T and the CTAs per SM the
 // kernel is compiled for are the table of teams.cuh).  The s = T ceil(n/T) - n
 // padding slots (j < 0) sit in the first block of T columns, which drops out
 // of the elimination after its first steps; in the last block they would be
