@@ -80,16 +80,17 @@ def measure(pm, stream: torch.cuda.Stream, reps: int = 2) -> tuple:
     return sec, float(max(free0 - free1, 1))
 
 
-def calibrate(mats: Sequence, stream: Optional[torch.cuda.Stream] = None):
+def calibrate(mats: Sequence, stream: Optional[torch.cuda.Stream] = None, reps: int = 2):
     """Timings and footprints the method itself generates, for training:
-    returns (features [B][8], measured [B][2], bounds [B][2])."""
+    returns (features [B][8], measured [B][2], bounds [B][2]); each time is
+    the mean of ``reps`` runs after a warm one."""
     st = stream or torch.cuda.Stream()
     measure(mats[0], st)  # warm-up: module load, kernel attributes
     X, Y, Bd = [], [], []
     for pm in mats:
         s = shape_of(pm)
         X.append(features(s))
-        Y.append(measure(pm, st))
+        Y.append(measure(pm, st, reps=reps))
         Bd.append(analytic(s))
     return np.stack(X), np.array(Y, dtype=np.float64), np.array(Bd, dtype=np.float64)
 
