@@ -175,9 +175,23 @@ def variable_order(n: int, degs: Sequence[int]) -> List[int]:
     lowest degree first when its matrix order is materialized by default (the
     first variable's pass writes every evaluated matrix, and a short input is
     the cheapest to transform), last when fused (the last variable is the
-    one evaluated inside the determinant kernel).  Ties keep the given order."""
+    one evaluated inside the determinant kernel).  Ties keep the given order
+    in the first case and come out reversed in the second."""
     order = sorted(range(len(degs)), key=lambda v: (int(degs[v]), v))
     return order if n >= BATCH_MATERIALIZE_N else order[::-1]
+
+
+def unpermute_output(vals: Sequence[int], order: Sequence[int], box: Sequence[int]) -> List[int]:
+    """Output coefficients computed with the variables in ``order`` (lex over
+    ``box``, the extents D_v + 1 in that order) put back in the caller's
+    variable order: the inverse of the transposition ``permute_coeffs``
+    applies to the input."""
+    if list(order) == sorted(order):
+        return list(vals)
+    arr = np.empty(len(vals), dtype=object)
+    arr[:] = list(vals)
+    inv = [list(order).index(v) for v in range(len(order))]
+    return arr.reshape(tuple(int(b) for b in box)).transpose(inv).reshape(-1).tolist()
 
 
 def permute_coeffs(coeffs: np.ndarray, degs: Sequence[int], order: Sequence[int]) -> np.ndarray:
@@ -378,13 +392,8 @@ class BatchedRunner:
             C, W = int(info.C), int(info.W)
             vals = limbs_to_ints(host[lo[j]:lo[j + 1]].reshape(C, W), W)
             order = self.orders[j]
-            if list(order) != sorted(order):  # back to the caller's variable order
-                box = tuple(int(info.D[v]) + 1 for v in range(len(order)))
-                arr = np.empty(C, dtype=object)
-                arr[:] = vals
-                inv = [order.index(v) for v in range(len(order))]
-                vals = arr.reshape(box).transpose(inv).reshape(-1).tolist()
-            out.append(vals)
+            box = tuple(int(info.D[v]) + 1 for v in range(len(order)))
+            out.append(unpermute_output(vals, order, box))  # the caller's variable order
         return out
 
     def release_buffers(self) -> None:
