@@ -293,11 +293,12 @@ int polydet_batch_set_mode(polydet_batch_t batch, int n, int mode);
 /* Chunk budget of the materialized mode in words (>= 1; the workspace size
  * changes: query again).  Not during a graph capture. */
 int polydet_batch_set_chunk_words(polydet_batch_t batch, uint64_t words);
-/* Test hook for failure detection, off by default.  With on = 1 the fused
- * kernels withhold the bulk copies of their staged rows (those that would be
- * issued), so each CTA's bounded wait for them runs out after about one
- * second; the CTA then sets POLYDET_STATUS_TIMEOUT in its job plan's status
- * word (polydet_batch_sync_status returns POLYDET_ETIMEOUT) and ends, and the
+/* Test hook for failure detection (no counterpart in the paper), off by
+ * default.  With on = 1 the fused kernels withhold the bulk copies of their
+ * staged rows (those that would be issued), so each CTA's bounded wait for
+ * them runs out after about one second; the CTA then sets
+ * POLYDET_STATUS_TIMEOUT in its job plan's status word
+ * (polydet_batch_sync_status returns POLYDET_ETIMEOUT) and ends, and the
  * determinant values of those items are not written.  on = 0 restores normal
  * operation.  Not during a graph capture (uploads the segment tables). */
 int polydet_batch_test_drop_copies(polydet_batch_t batch, int on);
