@@ -223,10 +223,12 @@ class OraclePool:
         self.pool.map(_oracle_det, self.eligible[:self.workers])
         self.next = 0
 
-    def sample(self, seconds: float):
+    def window(self, seconds: float):
         """Keep every worker busy with the next member (cycling through the
-        eligible ones) until ``seconds`` have passed, then wait for the
-        members in flight.  Returns (members done, elapsed seconds)."""
+        eligible ones) for ``seconds`` of wall time.  Returns the completion
+        times (seconds from the start) of the members finished inside the
+        window; members still running when it ends are not counted (close()
+        ends them), so the window's length bounds the run."""
         import queue
         done_q = queue.SimpleQueue()
         t0 = time.perf_counter()
@@ -238,17 +240,23 @@ class OraclePool:
 
         for _ in range(self.workers):
             submit()
-        inflight, done = self.workers, 0
-        while inflight:
-            r = done_q.get()
-            inflight -= 1
+        times = []
+        while True:
+            left = seconds - (time.perf_counter() - t0)
+            if left <= 0:
+                break
+            try:
+                r = done_q.get(timeout=left)
+            except queue.Empty:
+                break
             if isinstance(r, BaseException):
                 raise r
-            done += 1
-            if time.perf_counter() - t0 < seconds:
-                submit()
-                inflight += 1
-        return done, time.perf_counter() - t0
+            t = time.perf_counter() - t0
+            if t > seconds:
+                break
+            times.append(t)
+            submit()
+        return times
 
     def close(self):
         self.pool.terminate()
@@ -260,15 +268,12 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     mats = synth.batched(args.seed, args.count)
-    per_step = max(2.0, args.cpu_seconds / 2)
+    # the steps are consecutive slices of one window of at most two minutes
+    el = min(args.steps * max(2.0, args.cpu_seconds / 2), 120.0)
+    per_step = el / args.steps
     pool = OraclePool(mats)
     try:
-        done = 0
-        el = 0.0
-        for _ in range(args.steps):
-            d, e = pool.sample(per_step)
-            done += d
-            el += e
+        done = len(pool.window(el))
     finally:
         pool.close()
     workers = pool.workers
@@ -280,7 +285,7 @@ def run_reference(args, world, rank):
         "vs_baseline": None, "dtype": "python int (exact)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "seed": args.seed, "sample": "cost-capped members in seed order"},
         "cpu_baseline": {"value": value, "unit": "exact dets/s", "cores": workers, "kind": "oracle",
-                         "sample": f"{done} members over {args.steps} steps of ~{per_step:.0f} s, one per "
+                         "sample": f"{done} members finished in {args.steps} steps of {per_step:.1f} s, one per "
                                    f"process on {workers} cores: members of the seeded batch in order "
                                    "whose n^3*prod(n d_v+1) <= 2e6 (small ones; larger ones are out of "
                                    "reach of the Python oracle)"},
@@ -648,7 +653,8 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         pool = OraclePool(mats)
         try:
-            done, el = pool.sample(args.cpu_seconds)
+            el = args.cpu_seconds
+            done = len(pool.window(el))
         finally:
             pool.close()
         skipped, workers = pool.skipped, pool.workers
