@@ -118,7 +118,7 @@ def test_trained_network_beats_the_analytic_bound_on_measured_jobs():
     print("median |log error| time/mem: mlp", e_mlp, "calibrated bound", e_ana, "bound", e_raw)
     assert np.all(e_mlp < e_ana)
     assert np.all(e_mlp < e_raw)
-    # the judge: never below the analytic lower bound
+    # the analytic bound judges the network: no prediction falls below it
     assert np.all(pred >= Bd[test] * (1 - 1e-9))
 
 
