@@ -148,7 +148,10 @@ __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
 // twiddle products and a register DFT of size LP per LP outputs, in which
 // the LP - Lin inputs that are zero are folded away at compile time.  A
 // thread owns CPT columns (blockDim apart, so every store of a row stays
-// coalesced) and loads each coset's twiddles once for all of them.
+// coalesced) and loads each coset's twiddles once for all of them.  With one
+// column per thread the grid may instead run over (item, column, coset group)
+// triples (TxArgs::flat_items): short rows then fill whole CTAs, and a pass
+// with few columns in all spreads each column's cosets over several threads.
 __device__ __forceinline__ uint32_t tw_pow(const uint32_t *tw, int k) {
   return __ldg(tw + k);  // w^k * R for 0 <= k < N: the table holds the whole circle
 }
