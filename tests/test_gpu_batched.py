@@ -255,7 +255,7 @@ def test_withheld_bulk_copies_time_out_and_are_reported():
     dt = time.perf_counter() - t0
     status = r.batch.sync_status(st)  # reads and clears every job's word
     assert status & 0x2, status
-    assert 0.5 < dt < 60, dt
+    assert 0.01 < dt < 60, dt  # the wait is bounded by time (1 s) or by a poll count
     r.batch.test_drop_copies(False)
     r.compute(st)
     r.download(st)
