@@ -4,7 +4,10 @@ checked equal: a small self-contained workload for profiling one kernel, e.g.
     python -m paper_2010_12117_gb300.case --n 24 --degs 3,3
 
 runs condense_kernel<24, ...> on 73 x 73 nodes per prime (plain form, then
-the batched form in the chosen mode) and prints the job's sizes.
+the batched form in the chosen mode) and prints the job's sizes.  Other
+stages: ``--stage eval`` / ``--stage crt`` run one stage alone on inputs
+larger than L2, and ``--stage batched`` runs one profiled step of the
+256-matrix batched workload (between cudaProfilerStart and Stop).
 """
 from __future__ import annotations
 
