@@ -32,10 +32,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("exact poly determinants/sec and mod-p n×n dets/sec; IMAD % and HBM GB/s of peak")
 # DRAM traffic of condense_kernel measured by ncu (read + write over the
-# algorithmic bytes 4 n^2 + 4 per determinant; n = 24 capture, see
-# profiles/condense_kernel_n24_case.md), valid only for the code it was taken
-# on: digests of the kernel's sources with comments and blank space removed;
-# the bench reports traffic null once they change.
+# algorithmic bytes 4 n^2 + 4 per determinant, from one capture of a single
+# 24 x 24 launch), valid only for the code it was taken on: digests of the
+# kernel's sources with comments and blank space removed; the bench reports
+# traffic null once they change.
 CONDENSE_TRAFFIC = {"ratio": 1.0161, "sources": {"paper_2010_12117_gb300/csrc/condense.cuh": "b1f535722ef6c820",
                                                 "paper_2010_12117_gb300/csrc/modarith.cuh": "df18107d8f4cddb4",
                                                 "paper_2010_12117_gb300/csrc/teams.cuh": "62d88c4a443f98e8"}}
@@ -201,11 +201,10 @@ def oracle_cost(pm) -> float:
 
 
 def _oracle_det(item):
-    """One member through the oracle (runs in a pool worker)."""
+    """One member through the oracle (runs in a pool worker): (index, det)."""
     from oracle import bareiss
-    coeffs, degs = item
-    bareiss.det_packed(coeffs, degs)
-    return 1
+    idx, coeffs, degs = item
+    return idx, bareiss.det_packed(coeffs, degs)
 
 
 class OraclePool:
@@ -216,7 +215,8 @@ class OraclePool:
 
     def __init__(self, mats, cap: float = 2e6, workers: int = 0):
         import multiprocessing
-        self.eligible = [(pm.coeffs.tolist(), tuple(pm.degs)) for pm in mats if oracle_cost(pm) <= cap]
+        self.eligible = [(i, pm.coeffs.tolist(), tuple(pm.degs)) for i, pm in enumerate(mats)
+                         if oracle_cost(pm) <= cap]
         self.skipped = len(mats) - len(self.eligible)
         self.workers = workers or os.cpu_count() or 1
         self.pool = multiprocessing.get_context("spawn").Pool(self.workers)
@@ -228,7 +228,9 @@ class OraclePool:
         eligible ones) for ``seconds`` of wall time.  Returns the completion
         times (seconds from the start) of the members finished inside the
         window; members still running when it ends are not counted (close()
-        ends them), so the window's length bounds the run."""
+        ends them), so the window's length bounds the run.  ``self.results``
+        maps each finished member's index to the oracle's determinant."""
+        self.results = {}
         import queue
         done_q = queue.SimpleQueue()
         t0 = time.perf_counter()
@@ -255,6 +257,7 @@ class OraclePool:
             if t > seconds:
                 break
             times.append(t)
+            self.results[r[0]] = r[1]
             submit()
         return times
 
@@ -539,6 +542,7 @@ def run_ours(args, world, rank, local):
     t0 = time.perf_counter()
     runner.run_pipelined(args.steps, st, cs)
     e2e_ms = 1e3 * (time.perf_counter() - t0)
+    runner.check_status(st)  # the pipelined runs' status word (raises when set)
     e2e_total = max_over_ranks(e2e_ms, world)
     e2e_value = exact_all * args.steps / (e2e_total * 1e-3)
     batched_results = runner.results()
@@ -576,6 +580,7 @@ def run_ours(args, world, rank, local):
         flush.fill_(4)
     plain.compute(st, ptimer)
     torch.cuda.synchronize()
+    plain.check_status(st)
     plain_stage_ms = ptimer.ms()
     # algorithmic bytes of the condensation launches: 4 n^2 + 4 per determinant
     cond_bytes = sum(float(pl.P * pl.G) * (4 * pm.n * pm.n + 4) for pm, pl in zip(plain.mats, plain.plans))
@@ -658,10 +663,16 @@ def run_ours(args, world, rank, local):
         finally:
             pool.close()
         skipped, workers = pool.skipped, pool.workers
+        # every member the oracle finished is also a parity check of the
+        # batched form's output for it (identical integers required)
+        checked = {i: d == batched_results[i] for i, d in pool.results.items()}
         cpu = {"value": done / el, "unit": "exact dets/s", "cores": workers, "kind": "oracle",
                "sample": f"{done} members of the same seeded batch in order, skipping {skipped} whose "
                          f"n^3*prod(n d_v+1) > 2e6, {el:.1f} s, one member per Python process on "
-                         f"{workers} cores (small members only: larger ones are out of reach of the oracle)"}
+                         f"{workers} cores (small members only: larger ones are out of reach of the oracle)",
+               "gpu_output_checked": {"distinct_members": len(checked),
+                                      "bit_exact": sum(checked.values()),
+                                      "mismatched": [i for i, ok in checked.items() if not ok]}}
 
     line = {
         "metric": METRIC, "value": value, "unit": "exact dets/s", "n_gpus": world,

@@ -60,6 +60,10 @@ extern "C" {
 /* Bits of the device status word (polydet_sync_status). */
 #define POLYDET_STATUS_BOUND 0x1u   /* interpolation tail was nonzero */
 #define POLYDET_STATUS_TIMEOUT 0x2u /* a bounded wait gave up         */
+/* A bulk copy was still outstanding after a timed-out CTA's last bounded
+ * wait: it may yet land in shared memory another CTA owns, so the CUDA
+ * context is no longer trustworthy and should be torn down. */
+#define POLYDET_STATUS_INFLIGHT 0x4u
 
 /* Limits. */
 #define POLYDET_MAX_N 32          /* matrix order                          */
@@ -279,7 +283,9 @@ int polydet_batch_destroy(polydet_batch_t batch);
 int polydet_batch_query(polydet_batch_t batch, polydet_batch_info *info);
 /* Host `out[njobs + 1]` word offsets of buffer `which` (POLYDET_OFF_*). */
 int polydet_batch_offsets(polydet_batch_t batch, int which, int64_t *out);
-/* The plan of job `job` (owned by the batch; do not destroy). */
+/* The plan of job `job` (owned by the batch; do not destroy).  Every job plan
+ * of a batch reports into one status word, the batch's: polydet_sync_status
+ * on a job plan reads and clears the whole batch's status. */
 int polydet_batch_job_plan(polydet_batch_t batch, int job, polydet_plan_t *plan_out);
 /* CTA size (multiple of 32 and of the lanes per determinant, <= 128) of the
  * fused kernel for matrix order n; the autotuner's knob.  Not during a
@@ -327,7 +333,8 @@ int polydet_batch_interp(polydet_batch_t batch, const uint32_t *detvals_dev,
 /* Stage 4: Garner CRT per job (Sec. 3.4). */
 int polydet_batch_crt(polydet_batch_t batch, const uint32_t *residues_dev, uint32_t *limbs_dev,
                       void *stream);
-/* OR of every job's status word (synchronises; clears them). */
+/* The batch's status word, the OR of what any job reported (synchronises
+ * `stream` and clears it). */
 int polydet_batch_sync_status(polydet_batch_t batch, void *stream, uint32_t *status_out);
 
 /* ------------------------------------------------------------------------

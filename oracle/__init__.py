@@ -22,7 +22,8 @@ that each function can be read against the paper by eye:
 * ``predict``     - the run-time prediction formula of Sec. 5.
 
 Pins (tests marked ``not gpu``) tie each function to values the paper prints
-or the mathematics fixes; the one function without such a pin is
-``modular.count_ntt_primes_after`` (the prime-count table of Sec. 4.2), which
-is **parity unpinned**: the paper's counting rule cannot be recovered exactly.
+or the mathematics fixes.  ``modular.count_ntt_primes_after`` is pinned by
+hand-counted cases and an independent count; only its comparison with the
+printed prime-count table of Sec. 4.2 is unpinned, because the paper's
+counting rule cannot be recovered exactly.
 """

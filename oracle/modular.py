@@ -274,8 +274,10 @@ def to_limbs(X: int, W: int) -> List[int]:
 
 
 def count_ntt_primes_after(start: int, count: int, qs: Sequence[int]) -> Dict[int, int]:
-    """Among the first ``count`` primes above ``start``, how many satisfy
-    2^q | p - 1, for each q (the table of Sec. 4.2).  PARITY UNPINNED: the
+    """Among the first ``count`` primes strictly above ``start``, how many
+    satisfy 2^q | p - 1, for each q (the quantity tabulated in Sec. 4.2).
+    The function is pinned (hand-counted cases and an independent count);
+    only its comparison with the printed table is unpinned, because the
     paper's exact counting rule is not recoverable from its text."""
     out = {q: 0 for q in qs}
     p = start

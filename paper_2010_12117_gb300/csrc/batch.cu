@@ -59,6 +59,9 @@ struct polydet_batch_s {
   cudaStream_t fan[kFan] = {};
   cudaEvent_t fev[kFan + 1] = {};
   uint64_t scratch_stride = 0;
+  // one status word for every job of the batch (each job plan points at
+  // it), so that reading the batch's status is one copy, not one per job
+  uint32_t *d_status = nullptr;
 };
 
 static int fan_begin(polydet_batch_s *b, cudaStream_t st) {
@@ -109,6 +112,7 @@ static void update_ws(polydet_batch_s *b) {
 static void destroy_batch(polydet_batch_s *b) {
   if (!b) return;
   for (auto p : b->plans) polydet_plan_destroy(p);
+  cudaFree(b->d_status);
   for (int n = 0; n <= POLYDET_MAX_N; ++n) cudaFree(b->d_segs[n]);
   for (auto e : b->ev)
     if (e) cudaEventDestroy(e);
@@ -166,6 +170,11 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
     delete b;
     return POLYDET_ECUDA;
   }
+  if (cudaMalloc((void **)&b->d_status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(b->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+    destroy_batch(b);
+    return POLYDET_ENOMEM;
+  }
   b->coeff_off.assign(1, 0);
   b->part_off.assign(1, 0);
   b->det_off.assign(1, 0);
@@ -183,6 +192,9 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
       destroy_batch(b);
       return rc;
     }
+    cudaFree(pl->d_status);  // the job reports into the batch's word
+    pl->d_status = b->d_status;
+    pl->status_shared = 1;
     b->plans.push_back(pl);
     const int k = pl->nvars;
     const int L = pl->d[k - 1] + 1;
@@ -489,15 +501,6 @@ extern "C" int polydet_batch_crt(polydet_batch_t b, const uint32_t *residues, ui
 
 extern "C" int polydet_batch_sync_status(polydet_batch_t b, void *stream, uint32_t *status_out) {
   if (!b) return POLYDET_EINVAL;
-  uint32_t all = 0;
-  int worst = POLYDET_OK;
-  for (auto pl : b->plans) {
-    uint32_t s = 0;
-    int rc = polydet_sync_status(pl, stream, &s);
-    all |= s;
-    if (rc == POLYDET_ECUDA) return rc;
-    if (rc && !worst) worst = rc;
-  }
-  if (status_out) *status_out = all;
-  return worst;
+  // every job plan shares the batch's word: reading one plan reads them all
+  return polydet_sync_status(b->plans[0], stream, status_out);
 }

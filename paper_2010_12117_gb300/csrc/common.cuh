@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/polydet.h"
 #include "modarith.cuh"
 #include "teams.cuh"
@@ -66,6 +68,7 @@ struct polydet_plan_s {
   uint32_t *d_mhalf;      // [W] (M-1)/2
   uint32_t *d_mfull;      // [W] M
   uint32_t *d_status;     // 1 word
+  int status_shared;      // 1: d_status belongs to a batch (one word for all its jobs)
   uint64_t eval_ws_words;   // caller scratch per prime for polydet_eval
   uint64_t interp_ws_words; // caller scratch per prime for polydet_interp
   int tw_off[POLYDET_MAX_VARS];
@@ -81,6 +84,25 @@ void pd_set_error(const char *what, cudaError_t e);
       return POLYDET_ECUDA;                  \
     }                                        \
   } while (0)
+
+// Per-device one-time set-up of a call site (kernel attributes such as the
+// dynamic shared-memory limit are per device): runs `set` the first time the
+// call site runs with a given device current, under a lock.
+struct PdPerDevice {
+  std::mutex mu;
+  bool done[64] = {};
+};
+template <class F>
+int pd_once_per_device(PdPerDevice &pd, F &&set) {
+  int dev = 0;
+  PD_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return POLYDET_EINVAL;
+  std::lock_guard<std::mutex> lock(pd.mu);
+  if (pd.done[dev]) return POLYDET_OK;
+  const int rc = set();
+  if (rc == POLYDET_OK) pd.done[dev] = true;
+  return rc;
+}
 
 // Launchers implemented in separate translation units.
 // Where node g's evaluated matrix sits: entry e of node g of prime slot q at

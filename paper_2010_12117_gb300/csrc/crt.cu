@@ -204,11 +204,12 @@ extern "C" int polydet_crt(polydet_plan_t pl, const uint32_t *residues, uint32_t
   if (pl->P <= 32 && pl->W <= pl->P) return launch_crt_p<1>(pl, residues, limbs, (cudaStream_t)stream);
   const int threads = 128;
   const size_t smem = (size_t)(pl->P + pl->W) * threads * sizeof(uint32_t);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PdPerDevice attr;
+  int rc = pd_once_per_device(attr, [] {
     PD_CUDA(cudaFuncSetAttribute(crt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+    return POLYDET_OK;
+  });
+  if (rc) return rc;
   const unsigned blocks = (unsigned)((pl->C + threads - 1) / threads);
   crt_kernel<<<blocks, threads, smem, (cudaStream_t)stream>>>(residues, limbs, pl->C, pl->P, pl->W,
                                                                pl->d_mod, pl->d_garner, pl->d_mhalf,

@@ -17,7 +17,10 @@
 //  0. the Q rows its nodes need (about S / M_k + 1, contiguous) reach shared
 //     memory by one bulk copy that thread 0 started while the CTA computed
 //     the previous item (two buffers, one mbarrier each; a wait that runs
-//     out after a second sets POLYDET_STATUS_TIMEOUT and ends the CTA).
+//     out after a second sets POLYDET_STATUS_TIMEOUT and ends the CTA, after
+//     one more bounded wait for every copy it issued; a copy still
+//     outstanding then also sets POLYDET_STATUS_INFLIGHT, after which the
+//     host must treat the CUDA context as unusable and tear it down).
 //     Rows whose start or size is not a multiple of 16 bytes are copied by
 //     the CTA itself;
 //  1. a team of T lanes owns node g = (row, i): it forms x, the node's power
@@ -235,12 +238,18 @@ __global__ void __launch_bounds__(128) fused_kernel(const FusedSeg *__restrict__
       for (int w = threadIdx.x; w < f.words; w += bd) qsm[w] = __ldg(src + w);
     }
     if (__syncthreads_or(late)) {
-      // a copy did not land in time: report it, let the copy issued above
-      // land (bounded again), and stop this CTA
+      // a copy did not land in time: report it, give both copies that may
+      // still be in flight - this item's (when one was issued) and the next
+      // item's started above - one more bounded wait each, and stop this
+      // CTA.  If either is still outstanding after that, it could land in
+      // shared memory that a later CTA owns: POLYDET_STATUS_INFLIGHT tells
+      // the host that the context must not be trusted any more.
       if (threadIdx.x == 0) {
+        bool gone = true;
+        if (bulk == 1) gone &= pd_mbar_wait_bounded(&s_bar[cur], ((phase >> cur) & 1u) ^ 1u);
         if (nbuf == 2 && s_bulk[cur ^ 1] == 1)
-          pd_mbar_wait_bounded(&s_bar[cur ^ 1], (phase >> (cur ^ 1)) & 1u);
-        atomicOr(sg.status, POLYDET_STATUS_TIMEOUT);
+          gone &= pd_mbar_wait_bounded(&s_bar[cur ^ 1], (phase >> (cur ^ 1)) & 1u);
+        atomicOr(sg.status, POLYDET_STATUS_TIMEOUT | (gone ? 0u : POLYDET_STATUS_INFLIGHT));
       }
       return;
     }

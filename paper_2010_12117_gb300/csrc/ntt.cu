@@ -388,11 +388,12 @@ static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
   a.Ct = ct;
   a.logCt = ilog2(ct);
   size_t smem = (size_t)a.N * (ct + 1) * sizeof(uint32_t);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PdPerDevice attr;
+  int rc = pd_once_per_device(attr, [] {
     PD_CUDA(cudaFuncSetAttribute(coltx_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+    return POLYDET_OK;
+  });
+  if (rc) return rc;
   dim3 grid((unsigned)((ncols + ct - 1) / ct), (unsigned)items, (unsigned)nprimes);
   coltx_kernel<<<grid, 256, smem, st>>>(a);
   PD_CUDA(cudaGetLastError());
@@ -634,14 +635,15 @@ static int interp_nodes(polydet_plan_t pl, const uint32_t *detvals, int lo, int 
   const int k = pl->nvars, np = hi - lo;
   const uint64_t slot = pl->interp_ws_words / 2;
   constexpr size_t kMaxSmem = 200 * 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PdPerDevice attr;
+  const int arc = pd_once_per_device(attr, [] {
     PD_CUDA(cudaFuncSetAttribute(cinterp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PD_CUDA(cudaFuncSetAttribute(cinterp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PD_CUDA(cudaFuncSetAttribute(cinterp_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PD_CUDA(cudaFuncSetAttribute(cinterp_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-    attr_set = true;
-  }
+    return POLYDET_OK;
+  });
+  if (arc) return arc;
   const uint32_t *cur = detvals;
   int64_t cur_prime = pl->G;
   int t = 0;

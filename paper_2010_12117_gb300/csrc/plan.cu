@@ -246,7 +246,7 @@ static void free_plan(polydet_plan_s *pl) {
   cudaFree(pl->d_garner);
   cudaFree(pl->d_mhalf);
   cudaFree(pl->d_mfull);
-  cudaFree(pl->d_status);
+  if (!pl->status_shared) cudaFree(pl->d_status);
   cudaFree(pl->d_itab);
   delete pl;
 }

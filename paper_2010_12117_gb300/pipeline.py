@@ -4,7 +4,8 @@ For every prime: evaluation (polydet_eval), condensation
 (polydet_condense_batch), interpolation (polydet_interp); then mixed-radix
 CRT over all primes (polydet_crt).  Primes are processed in chunks sized to a
 device-memory budget; with a ``ResidueStore`` the per-prime residues are
-saved after each chunk and a rerun computes only the missing primes.
+saved after each chunk, once the device status word reads clean, and a
+rerun computes only the missing primes.
 """
 from __future__ import annotations
 
@@ -84,6 +85,12 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
             plan.condense(evals, lo, hi, detv, st)
             plan.interp(detv, lo, hi, residues[lo * plan.C:hi * plan.C], ws, st)
             if store is not None:
+                # a restart point is only as good as its residues: read the
+                # status word first, and persist nothing the device flagged
+                status = plan.sync_status(st)
+                if status:
+                    raise PolydetError(EBOUND, f"device status {status:#x} in primes [{lo}, {hi}); "
+                                               "nothing saved for them")
                 host = as_u32(residues[lo * plan.C:hi * plan.C])
                 for q in range(lo, hi):
                     store.save(q, host[(q - lo) * plan.C:(q - lo + 1) * plan.C])

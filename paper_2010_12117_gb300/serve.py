@@ -13,7 +13,10 @@ finishing wave does not synchronise the device while others run; the plan
 tables of finished waves are destroyed once the device is idle.
 
 A request's result does not depend on which wave it ran in: every job keeps
-its own plan (primes, grid) and buffers inside a wave.
+its own plan (primes, grid) and buffers inside a wave.  When a wave
+completes, its device status word is read before anything is returned; a
+wave whose word is set returns no results, and its jobs are counted as
+failed.
 """
 from __future__ import annotations
 
@@ -37,6 +40,7 @@ class Done:
     finish: float
     coeffs: List[int]
     wave: int
+    ok: bool = True  # False: the wave's device status word was set; no result
 
 
 @dataclass
@@ -51,12 +55,13 @@ class ServeReport:
     modp_dets: int
     peak_pred_mem: float
     done: List[Done] = field(default_factory=list)
+    failed: int = 0  # jobs of waves whose device status word was set
 
     def summary(self) -> dict:
         return {"jobs": self.jobs, "waves": self.waves, "wall_s": self.wall_s,
                 "p50_ms": self.p50_ms, "p99_ms": self.p99_ms, "mean_ms": self.mean_ms,
                 "exact_dets_per_s": self.exact_dets_per_s, "modp_dets": self.modp_dets,
-                "peak_predicted_mem_bytes": self.peak_pred_mem}
+                "peak_predicted_mem_bytes": self.peak_pred_mem, "failed_jobs": self.failed}
 
 
 def measure(pm, stream: torch.cuda.Stream, reps: int = 2) -> tuple:
@@ -119,6 +124,7 @@ class Server:
         peak = 0.0
         waves = 0
         modp = 0
+        failed = 0
         t0 = time.perf_counter()
         while nxt < len(order) or pending or inflight:
             now = time.perf_counter() - t0
@@ -129,9 +135,19 @@ class Server:
             for w in list(inflight):
                 if w["event"].query():
                     fin = time.perf_counter() - t0
-                    res = w["runner"].results() if keep_results else [[] for _ in w["jobs"]]
+                    # the wave's stream is idle: reading its status word is
+                    # one small copy; a set word (a bounded wait that ran
+                    # out, a degree bound that did not hold) means its limbs
+                    # are not the determinants, so none is returned
+                    status = w["runner"].batch.sync_status(self.streams[w["slot"]])
+                    if status:
+                        failed += len(w["jobs"])
+                        res = [[] for _ in w["jobs"]]
+                    else:
+                        res = w["runner"].results() if keep_results else [[] for _ in w["jobs"]]
                     for j, coeffs in zip(w["jobs"], res):
-                        done.append(Done(j, arrivals[j].t, w["start"], fin, coeffs, w["id"]))
+                        done.append(Done(j, arrivals[j].t, w["start"], fin, coeffs, w["id"],
+                                         ok=not status))
                     w["runner"].release_buffers()
                     graveyard.append(w["runner"])
                     mem_used -= w["mem"]
@@ -188,4 +204,4 @@ class Server:
         done.sort(key=lambda d: d.idx)
         return ServeReport(len(done), waves, wall, float(np.percentile(lat, 50)),
                            float(np.percentile(lat, 99)), float(lat.mean()),
-                           len(done) / max(wall, 1e-9), modp, peak, done)
+                           len(done) / max(wall, 1e-9), modp, peak, done, failed)

@@ -43,3 +43,21 @@ def random_residue_mats(rng, P, G, n, primes, zero_frac=0.0):
             m[rng.random((G, n, n)) < zero_frac] = 0
         out[q] = m
     return out
+
+
+def oracle_check_member(args):
+    """One GPU result checked by the oracle, in a worker process (no torch
+    import): bit-exact against O2 when ``exact``, else the Schwartz-Zippel
+    certificate with ``trials`` points.  Returns (kind, ok, seconds)."""
+    import time
+    from oracle import bareiss, certificate, plan
+    coeffs, degs, got, exact, trials = args
+    t = time.perf_counter()
+    if exact:
+        ok = bareiss.det_packed(coeffs, degs) == got
+        kind = "exact"
+    else:
+        D = plan.det_degree_bound(len(coeffs), degs)
+        ok = certificate.check(coeffs, degs, got, D, trials=trials)
+        kind = "certified"
+    return kind, ok, time.perf_counter() - t

@@ -75,7 +75,7 @@ def test_sparse_12x12_xyz_full_size(nprimes):
         assert got.coeffs[int(i)] == int(v), i
     assert _digest(got.coeffs) == g["sha256"]
     if nprimes is None:
-        assert certificate.check(pm.coeffs.tolist(), pm.degs, got.coeffs, got.D, trials=2)
+        assert certificate.check(pm.coeffs.tolist(), pm.degs, got.coeffs, got.D, trials=8)
     else:
         assert got.P == 20
 
@@ -167,7 +167,7 @@ def test_batched_members_certified():
         if cost < 3e6:
             assert got.coeffs == bareiss.det_packed(pm.coeffs.tolist(), pm.degs), pm.name
         else:
-            assert certificate.check(pm.coeffs.tolist(), pm.degs, got.coeffs, got.D, trials=2), pm.name
+            assert certificate.check(pm.coeffs.tolist(), pm.degs, got.coeffs, got.D, trials=8), pm.name
 
 
 def test_six_variables_and_long_univariate_grids():

@@ -58,9 +58,10 @@ def test_paper_prediction_example():
 
 
 def test_prime_count_table_reported():
-    """Parity unpinned (the paper's rule is ambiguous): only checks that our
-    counts fall within a factor of two of the printed ones where the
-    printed counts are large, and decrease with q."""
+    """The comparison with Table 3 itself stays unpinned (the paper's counting
+    rule is ambiguous): only checks that our counts fall within a factor of
+    two of the printed ones where the printed counts are large, and decrease
+    with q.  The counting function is pinned by the two tests below."""
     ex = PAPER["prime_counts"]
     qs = [int(q) for q in ex["q_to_count"]]
     ours = modular.count_ntt_primes_after(ex["start"], 2000, qs)
@@ -69,6 +70,32 @@ def test_prime_count_table_reported():
         assert 0.5 < scaled[q] / ex["q_to_count"][str(q)] < 2.0
     vals = [ours[q] for q in sorted(qs)]
     assert vals == sorted(vals, reverse=True)
+
+
+def test_prime_count_hand_counted_cases():
+    """Counted by hand.  The first ten primes 2..29 have p - 1 =
+    1, 2, 4, 6, 10, 12, 16, 18, 22, 28: nine are even, four are multiples of
+    4 (p = 5, 13, 17, 29), one of 8 and of 16 (p = 17).  Counting starts
+    strictly above ``start``: after 17 come 19, 23, 29 (p - 1 = 18, 22, 28),
+    so 17 itself (16 | p - 1) must not be counted."""
+    assert modular.count_ntt_primes_after(0, 10, [1, 2, 3, 4]) == {1: 9, 2: 4, 3: 1, 4: 1}
+    assert modular.count_ntt_primes_after(17, 3, [1, 2, 3, 4]) == {1: 3, 2: 1, 3: 0, 4: 0}
+    assert modular.count_ntt_primes_after(16, 1, [4]) == {4: 1}
+
+
+def test_prime_count_matches_an_independent_count():
+    """The first 2000 primes above 10^9 (the window of Sec. 4.2) from sympy's
+    sieve, and for each the exponent of 2 in p - 1 read off its lowest set
+    bit; the oracle's count must agree for every q exactly."""
+    sympy = pytest.importorskip("sympy")
+    start, count = 10 ** 9, 2000
+    ps = list(sympy.primerange(start + 1, start + 60000))
+    assert len(ps) >= count
+    ps = ps[:count]
+    val2 = [((p - 1) & -(p - 1)).bit_length() - 1 for p in ps]
+    qs = [1, 2, 3, 6, 7, 8, 9, 12, 13, 16]
+    want = {q: sum(1 for v in val2 if v >= q) for q in qs}
+    assert modular.count_ntt_primes_after(start, count, qs) == want
 
 
 # --------------------------------------------------------------------------
@@ -405,6 +432,40 @@ def test_certificate_accepts_truth_and_rejects_a_planted_error():
     j = next(i for i, c in enumerate(bad) if c)
     bad[j] += 1
     assert not certificate.check(pm.coeffs.tolist(), pm.degs, bad, D)
+
+
+@pytest.mark.parametrize("degs", [(0,), (5,), (3, 0), (2, 4), (1, 2, 3), (2, 0, 1, 1)])
+def test_certificate_horner_equals_the_monomial_sum(degs):
+    """The nested-Horner evaluation of a dense lex polynomial equals the plain
+    sum over its monomials (every exponent vector, every axis order)."""
+    rng = np.random.default_rng(sum(degs) + 7 * len(degs))
+    q = certificate.Q61
+    size = int(np.prod([d + 1 for d in degs]))
+    for _ in range(4):
+        vec = [int(x) for x in rng.integers(-2 ** 62, 2 ** 62, size)]
+        vec[int(rng.integers(0, size))] = 3 ** 90  # a big-integer coefficient
+        point = [int(x) for x in rng.integers(1, q - 1, len(degs))]
+        box = certificate._box(vec, degs, q)
+        assert certificate._eval_horner(box, degs, point, q) == certificate._eval_dense(vec, degs, point, q)
+
+
+def test_certificate_catches_every_single_coefficient_error():
+    """A wrong claim that differs from the truth in any one coefficient (each
+    position tried) fails the certificate; so do a transposed output and a
+    sign flip."""
+    rng = np.random.default_rng(32)
+    pm = rand_matrix(rng, 3, (1, 2), 0.8, -50, 51)
+    det = bareiss.det_packed(pm.coeffs.tolist(), pm.degs)
+    D = plan.det_degree_bound(3, pm.degs)
+    assert certificate.check(pm.coeffs.tolist(), pm.degs, det, D, trials=2)
+    for j in range(len(det)):
+        bad = list(det)
+        bad[j] -= 1
+        assert not certificate.check(pm.coeffs.tolist(), pm.degs, bad, D, trials=2), j
+    assert not certificate.check(pm.coeffs.tolist(), pm.degs, [-c for c in det], D, trials=2)
+    tr = np.array(det, dtype=object).reshape(D[0] + 1, D[1] + 1)[::-1, :].reshape(-1).tolist()
+    if tr != det:
+        assert not certificate.check(pm.coeffs.tolist(), pm.degs, tr, D, trials=2)
 
 
 def test_workload_generators_shapes():

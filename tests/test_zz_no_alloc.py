@@ -83,6 +83,7 @@ def test_static_scratch_interp_two_calls_on_a_second_shape():
         got = torch.zeros(P * pl.C, dtype=torch.int32, device="cuda")
         pl.interp_static(dv, 0, P, got)
         torch.cuda.synchronize()
+        assert pl.sync_status() == 0
         assert np.array_equal(as_u32(got), as_u32(want))
 
 
