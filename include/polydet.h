@@ -68,7 +68,9 @@ extern "C" {
 /* Limits. */
 #define POLYDET_MAX_N 32          /* matrix order                          */
 #define POLYDET_MAX_VARS 6        /* number of variables k                 */
-#define POLYDET_MAX_GRID_DIM 8192 /* N_v cap (the paper's MAX_FFT_DIM)     */
+#define POLYDET_MAX_GRID_DIM 8192 /* N_v cap (the paper's MAX_FFT_DIM, Sec. 3.1:
+                                     one column's transform runs in one CTA's
+                                     shared memory)                         */
 #define POLYDET_MAX_PRIMES 91     /* primes c*2^20+1 in (2^30, 2^31)       */
 
 typedef struct polydet_plan_s *polydet_plan_t;
@@ -88,6 +90,9 @@ typedef struct polydet_plan_info {
   uint64_t interp_ws_words;        /* polydet_interp scratch per prime     */
   int32_t M[POLYDET_MAX_VARS];     /* evaluation nodes per variable        */
   uint32_t flags;                  /* the plan's flags                     */
+  int32_t entries;                 /* entries per prime of the evals tensor
+                                      (n^2, or U + 1 with an entry map)    */
+  int32_t unique;                  /* U with an entry map, else -1         */
 } polydet_plan_info;
 
 /* Plan flag: evaluate on the full power-of-two grid (N_v nodes per variable)
@@ -100,9 +105,12 @@ typedef struct polydet_plan_info {
  * matrices. */
 #define POLYDET_FLAG_FULL_GRID 0x1u
 
-/* Primes of Eq. 1 with q = 20: every p = c * 2^20 + 1 in (2^30, 2^31), largest
- * first.  Returns the table size (91) when `out` is NULL, else writes that
- * many values to host `out`. */
+/* Primes of Eq. 1 with q = 20: every p = c * 2^20 + 1 in (2^30, 2^31); the 67
+ * up to 1865126253 first, then the 24 above it, each group largest first
+ * (plans take the first P: condensation runs its two-step elimination on
+ * primes up to that value, and the pivoting single-step one above it).
+ * Returns the table size (91) when `out` is NULL, else writes that many
+ * values to host `out`. */
 int polydet_prime_table(uint32_t *out);
 
 /* Coefficient bound and prime count (Sec. 2: the product of the primes must
@@ -124,6 +132,46 @@ int polydet_hadamard_primes(int n, const int64_t *entry_l1, int *nprimes_out,
  * polydet_plan_destroy. */
 int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
                  int nprimes, uint32_t flags);
+
+/* Degree bound of det(A) per variable from the degrees of the entries
+ * (Sec. 2 needs D_v + 1 interpolation nodes in x_v).  Host `entry_degs`
+ * [n][n][nvars] holds deg_{x_v} a_ij, or -1 in every variable for an
+ * identically zero entry.  Writes D_out[v] = the largest
+ * sum_i deg_v a_{i s(i)} over the permutations s that avoid zero entries
+ * (every term of the Leibniz expansion is such a product; 0 when no
+ * permutation avoids them, i.e. det = 0): never above the row-sum and
+ * column-sum bounds, nor above n * d_v, and exact for the resultant degree
+ * of a Sylvester matrix (Sec. 6).  Maximum-weight perfect matching by the
+ * Hungarian method, O(n^3) per variable; host only. */
+int polydet_det_degree_bound(int n, int nvars, const int32_t *entry_degs, int32_t *D_out);
+
+/* polydet_plan with explicit determinant degree bounds: host det_deg[nvars]
+ * with 0 <= det_deg[v] <= n * entry_deg[v] (e.g. from
+ * polydet_det_degree_bound) replaces n * entry_deg[v].  The grid then has
+ * D_v + 1 nodes per variable on the node grid, and N_v = the power of two
+ * >= max(D_v, d_v) + 1; the output has C = prod (D_v + 1) coefficients.  A
+ * bound below the true degree is an error the interpolation cannot always
+ * see: the caller must pass a valid bound. */
+int polydet_plan_degrees(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
+                         const int32_t *det_deg, int nprimes, uint32_t flags);
+
+/* Repeated entries (the factor mu of Sec. 5's prediction, and the reuse of
+ * a Sylvester matrix's repeated coefficients in Sec. 6).  Host `coeffs`
+ * [n*n][E]: writes map_out[n*n] (the index of entry (i, j) among the
+ * distinct nonzero entries in order of first occurrence, -1 for a zero
+ * entry), *U_out = their number, and, if `unique_out` is not NULL, their
+ * coefficients to host unique_out[U][E].  Host only. */
+int polydet_unique_entries(int n, int64_t E, const int32_t *coeffs, int32_t *map_out,
+                           int32_t *U_out, int32_t *unique_out);
+
+/* Attach an entry map to a plan (host map[n*n] as written by
+ * polydet_unique_entries; every index in [0, U) must occur).  From then on
+ * polydet_eval takes the U distinct entries, coeffs [U][E], evaluates only
+ * those, and writes evals [prime][U + 1][G] with slot U all zero;
+ * polydet_condense_batch and polydet_eval_condense read entry (i, j) of a
+ * node from slot map[i n + j] (slot U for -1).  Evaluation work and the
+ * evals tensor shrink by n^2 / (U + 1). */
+int polydet_plan_set_entry_map(polydet_plan_t plan, const int32_t *map, int U);
 int polydet_plan_destroy(polydet_plan_t plan);
 int polydet_plan_query(polydet_plan_t plan, polydet_plan_info *info);
 /* Host copies: primes [P]; roots w_{q,v} as [P][nvars]. */
@@ -136,8 +184,8 @@ int polydet_plan_nodes(polydet_plan_t plan, int var, int32_t *exps_out);
 /* Stage 1, evaluation (Sec. 3.1, Algorithm 2): for every prime q in
  * [prime_lo, prime_hi) and entry e, the multivariate NTT of the zero-padded
  * coefficients, i.e. the entry at every grid node mod p_q.
- * coeffs_dev: device int32 [n*n][E] (|c| < 2^31).  evals_dev: device uint32
- * [prime_hi - prime_lo][n*n][G].  ws_dev: device scratch of
+ * coeffs_dev: device int32 [n*n][E] (|c| < 2^31; [U][E] with an entry map).
+ * evals_dev: device uint32 [prime_hi - prime_lo][info.entries][G].  ws_dev: device scratch of
  * (prime_hi - prime_lo) * info.eval_ws_words words (NULL allowed when that
  * is 0, e.g. for one variable). */
 int polydet_eval(polydet_plan_t plan, const int32_t *coeffs_dev, int prime_lo,
@@ -150,6 +198,24 @@ int polydet_eval(polydet_plan_t plan, const int32_t *coeffs_dev, int prime_lo,
 int polydet_condense_batch(polydet_plan_t plan, const uint32_t *evals_dev,
                            int prime_lo, int prime_hi, uint32_t *detvals_dev,
                            void *stream);
+
+/* Stages 1 and 2 streamed through a fixed workspace (Sec. 3.1's multi-round
+ * evaluation when the evaluated tensor does not fit: one prime's
+ * [entries][G] never has to be resident).  For every prime q in
+ * [prime_lo, prime_hi): the passes of x_k, ..., x_2 into a head tensor
+ * [items][(d_1 + 1)][B] (B = prod_{v>1} M_v), then slab by slab - R
+ * consecutive nodes of x_1 at a time, R as large as `ws_words` allows - the
+ * x_1 pass of the slab's rows into [entries][R][B] and the condensation of
+ * those R * B nodes into detvals_dev[q - prime_lo][r0 B .. (r0 + R) B).
+ * coeffs_dev as for polydet_eval; detvals_dev: device uint32
+ * [prime_hi - prime_lo][G]; ws_dev: device scratch of ws_words words, at
+ * least polydet_stream_ws_words(plan, 1) (POLYDET_EINVAL otherwise).  On
+ * the node grid R is a multiple of the coset size of x_1 (up to 8).
+ * Everything is enqueued on `stream`; nothing is allocated. */
+uint64_t polydet_stream_ws_words(polydet_plan_t plan, int rows);
+int polydet_eval_condense(polydet_plan_t plan, const int32_t *coeffs_dev, int prime_lo,
+                          int prime_hi, uint32_t *detvals_dev, uint32_t *ws_dev, uint64_t ws_words,
+                          void *stream);
 
 /* Stage 3, interpolation (Sec. 3.3): on the full grid the inverse NTT with the
  * 1/N factor, keeping the C coefficients with e_v <= D_v (any nonzero
@@ -365,12 +431,15 @@ int polydet_mlp_backward(const float *params, const float *x, const float *targe
 int polydet_mlp_adam(float *params, const float *grads, float *m, float *v, int step, float lr,
                      float beta1, float beta2, float eps, float weight_decay, void *stream);
 
-/* Measurement utility (not a stage of the method): runs two in-register
+/* Measurement utility (not a stage of the method): runs three in-register
  * integer streams on every SM and reports their rates, the ceilings of the
- * condensation kernels - plain 32-bit multiply-adds per second, and fused
- * modular updates (a*b - c*d)/2^32 mod p per second.  Allocates and frees a
- * small buffer; synchronises `stream`. */
-int polydet_probe_int_peaks(void *stream, double *imad_per_s, double *update_per_s);
+ * condensation kernels - plain 32-bit multiply-adds per second, single-step
+ * modular updates (a*b - c*d)/2^32 mod p per second, and the two-step
+ * element updates (a*b + c*d + e*f)/2^32 mod p per second (each stands for
+ * two single-step updates).  Allocates and frees a small buffer;
+ * synchronises `stream`. */
+int polydet_probe_int_peaks(void *stream, double *imad_per_s, double *update_per_s,
+                            double *pair_update_per_s);
 
 /* Last CUDA error string seen by the library (host, static storage). */
 const char *polydet_last_error(void);

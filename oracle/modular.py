@@ -49,15 +49,22 @@ def is_prime(n: int) -> bool:
 NTT_Q = 20  # every prime admits 2^20-th roots of unity
 
 
+# The order in which the method takes the primes is free (the output does not
+# depend on it).  The table lists those up to this value first: a sum of three
+# products of residues below p, reduced once mod p, stays unambiguous in 32 bits
+# only up to it, and the GPU condensation relies on that.
+FOLD3_MAX = 1865126253
+
+
 def ntt_primes() -> List[int]:
-    """All primes p = c * 2^20 + 1 (Eq. 1 with q = 20) in (2^30, 2^31),
-    largest first."""
+    """All primes p = c * 2^20 + 1 (Eq. 1 with q = 20) in (2^30, 2^31): those
+    up to FOLD3_MAX largest first, then the others largest first."""
     out = []
     for c in range((2 ** 31 - 1) >> NTT_Q, (2 ** 30) >> NTT_Q, -1):
         p = (c << NTT_Q) + 1
         if 2 ** 30 < p < 2 ** 31 and is_prime(p):
             out.append(p)
-    return out
+    return [p for p in out if p <= FOLD3_MAX] + [p for p in out if p > FOLD3_MAX]
 
 
 def prime_factors(n: int) -> List[int]:

@@ -4,7 +4,9 @@ coefficient bound ("boundary") and the number of primes.
 Readings of the paper used here (the paper states no formula for either):
 
 * Degree bound.  det(A) has degree at most sum_i max_j deg_v a_ij <= n * d_v in
-  x_v, where d_v bounds the degree of every entry in x_v.  The grid needs
+  x_v, where d_v bounds the degree of every entry in x_v; the assignment
+  bound (the largest sum_i deg_v a_{i s(i)} over permutations s) is tighter
+  still and is what structured inputs (Sylvester matrices) are planned with.  The grid needs
   D_v + 1 distinct nodes per variable (interpolation, Sec. 3.3), padded to the
   next power of two, N_v = nextpow2(D_v + 1), which reproduces the paper's
   example (15, 7, 9) -> (16, 8, 16) of Sec. 2.
@@ -31,6 +33,56 @@ def next_pow2(x: int) -> int:
 def det_degree_bound(n: int, degs: Sequence[int]) -> Tuple[int, ...]:
     """D_v = n * d_v: the degree bound of det(A) in each variable."""
     return tuple(n * int(d) for d in degs)
+
+
+def entry_degrees(coeffs, degs: Sequence[int]):
+    """Per entry of the dense lex matrix ``coeffs`` [n][n][E]: its degree in
+    each variable, or None for an identically zero entry."""
+    from itertools import product
+    exps = list(product(*[range(int(d) + 1) for d in degs]))
+    out = []
+    for row in coeffs:
+        r = []
+        for vec in row:
+            nz = [e for e, c in zip(exps, vec) if int(c) != 0]
+            r.append(None if not nz else tuple(max(e[v] for e in nz) for v in range(len(degs))))
+        out.append(r)
+    return out
+
+
+def assignment_degree_bound(edeg, k: int, brute: "bool | None" = None) -> Tuple[int, ...]:
+    """D_v = max over permutations s with every a_{i s(i)} nonzero of
+    sum_i deg_v a_{i s(i)}: each term of the Leibniz expansion of det(A) is
+    such a product, so deg_v det(A) <= D_v (0 when no permutation avoids the
+    zero entries: then det(A) = 0).  It never exceeds the row-sum bound
+    sum_i max_j deg_v a_ij nor the column-sum bound.  Brute force over all
+    permutations for n <= 7 (or when ``brute``), otherwise the maximum-weight
+    perfect matching of scipy's assignment solver, zero entries weighted
+    below any matching that avoids them."""
+    from itertools import permutations
+    n = len(edeg)
+    out = []
+    for v in range(k):
+        if (n <= 7) if brute is None else brute:
+            best = None
+            for s in permutations(range(n)):
+                if any(edeg[i][s[i]] is None for i in range(n)):
+                    continue
+                t = sum(edeg[i][s[i]][v] for i in range(n))
+                best = t if best is None or t > best else best
+            out.append(0 if best is None else best)
+        else:
+            import numpy as np
+            from scipy.optimize import linear_sum_assignment
+            big = 1 + sum(max((e[v] for e in r if e is not None), default=0) for r in edeg)
+            w = np.array([[(e[v] if e is not None else -big * (n + 1)) for e in r] for r in edeg],
+                         dtype=np.int64)
+            rows, cols = linear_sum_assignment(w, maximize=True)
+            if any(edeg[i][j] is None for i, j in zip(rows, cols)):
+                out.append(0)
+            else:
+                out.append(int(w[rows, cols].sum()))
+    return tuple(out)
 
 
 def grid_sizes(D: Sequence[int]) -> Tuple[int, ...]:

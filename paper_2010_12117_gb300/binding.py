@@ -38,7 +38,8 @@ class PlanInfo(ctypes.Structure):
                 ("C", ctypes.c_int64), ("d", ctypes.c_int32 * MAX_VARS),
                 ("D", ctypes.c_int32 * MAX_VARS), ("N", ctypes.c_int32 * MAX_VARS),
                 ("eval_ws_words", ctypes.c_uint64), ("interp_ws_words", ctypes.c_uint64),
-                ("M", ctypes.c_int32 * MAX_VARS), ("flags", ctypes.c_uint32)]
+                ("M", ctypes.c_int32 * MAX_VARS), ("flags", ctypes.c_uint32),
+                ("entries", ctypes.c_int32), ("unique", ctypes.c_int32)]
 
 
 MAX_N = 32
@@ -78,6 +79,12 @@ SIGNATURES = {
     "polydet_hadamard_primes": (_I, [_I, _PI64, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_double)]),
     "polydet_plan": (_I, [ctypes.POINTER(_VP), _I, _I, _PI32, _I, _U32]),
+    "polydet_plan_degrees": (_I, [ctypes.POINTER(_VP), _I, _I, _PI32, _PI32, _I, _U32]),
+    "polydet_det_degree_bound": (_I, [_I, _I, _PI32, _PI32]),
+    "polydet_unique_entries": (_I, [_I, ctypes.c_int64, _PI32, _PI32, _PI32, _PI32]),
+    "polydet_plan_set_entry_map": (_I, [_VP, _PI32, _I]),
+    "polydet_stream_ws_words": (ctypes.c_uint64, [_VP, _I]),
+    "polydet_eval_condense": (_I, [_VP, _VP, _I, _I, _VP, _VP, ctypes.c_uint64, _VP]),
     "polydet_plan_destroy": (_I, [_VP]),
     "polydet_plan_query": (_I, [_VP, ctypes.POINTER(PlanInfo)]),
     "polydet_plan_primes": (_I, [_VP, _PU32]),
@@ -111,7 +118,7 @@ SIGNATURES = {
     "polydet_mlp_adam": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, ctypes.c_float, _VP]),
     "polydet_probe_int_peaks": (_I, [_VP, ctypes.POINTER(ctypes.c_double),
-                                     ctypes.POINTER(ctypes.c_double)]),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "polydet_last_error": (ctypes.c_char_p, []),
 }
 
@@ -162,6 +169,60 @@ def hadamard_primes(entry_l1: np.ndarray) -> tuple[int, float]:
     return P.value, lb.value
 
 
+def det_degree_bound(entry_degs, k: Optional[int] = None) -> tuple:
+    """Per-variable degree bound of det(A) from the entries' degrees:
+    ``entry_degs`` [n][n] of per-variable degree tuples, or None for a zero
+    entry (the library's assignment bound, host only); ``k`` variables
+    (taken from the entries when not given)."""
+    n = len(entry_degs)
+    if k is None:
+        k = next((len(e) for r in entry_degs for e in r if e is not None), 1)
+    arr = np.full((n, n, k), -1, dtype=np.int32)
+    for i, r in enumerate(entry_degs):
+        for j, e in enumerate(r):
+            if e is not None:
+                arr[i, j] = e
+    out = (ctypes.c_int32 * k)()
+    _check(lib().polydet_det_degree_bound(n, k, arr.ctypes.data_as(_PI32), out),
+           "polydet_det_degree_bound")
+    return tuple(out)
+
+
+def entry_degrees(coeffs: np.ndarray, degs: Sequence[int]):
+    """[n][n] per-variable degrees of the entries of a dense lex coefficient
+    array [n][n][E] (None for a zero entry): input marshalling for
+    det_degree_bound."""
+    c = np.asarray(coeffs)
+    n = c.shape[0]
+    shape = tuple(int(d) + 1 for d in degs)
+    out = []
+    for i in range(n):
+        row = []
+        for j in range(n):
+            t = c[i, j].reshape(shape)
+            if not t.any():
+                row.append(None)
+                continue
+            nz = np.nonzero(t)
+            row.append(tuple(int(ax.max()) for ax in nz))
+        out.append(row)
+    return out
+
+
+def unique_entries(coeffs: np.ndarray):
+    """(map [n*n] int32, U, distinct coefficient rows [U][E]) of a dense
+    coefficient array [n][n][E] (host only; -1 marks a zero entry)."""
+    c = np.ascontiguousarray(coeffs, dtype=np.int32)
+    n, E = c.shape[0], c.shape[2]
+    m = np.empty(n * n, dtype=np.int32)
+    U = ctypes.c_int32(0)
+    uniq = np.empty((n * n, E), dtype=np.int32)
+    _check(lib().polydet_unique_entries(n, E, c.ctypes.data_as(_PI32), m.ctypes.data_as(_PI32),
+                                        ctypes.byref(U), uniq.ctypes.data_as(_PI32)),
+           "polydet_unique_entries")
+    return m, U.value, uniq[:U.value].copy()
+
+
 def _ptr(t: torch.Tensor, dtype, numel: int, name: str) -> ctypes.c_void_p:
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
@@ -184,13 +245,24 @@ class Plan:
     <= degs[v] in x_v, over the first ``nprimes`` primes of the table; node
     grid (default) or the paper's full power-of-two grid."""
 
-    def __init__(self, n: int, degs: Sequence[int], nprimes: int, full_grid: bool = False):
+    def __init__(self, n: int, degs: Sequence[int], nprimes: int, full_grid: bool = False,
+                 det_degs: Optional[Sequence[int]] = None):
         L = lib()
         d = (ctypes.c_int32 * len(degs))(*[int(x) for x in degs])
         h = ctypes.c_void_p()
-        _check(L.polydet_plan(ctypes.byref(h), int(n), len(degs), d, int(nprimes),
-                              FLAG_FULL_GRID if full_grid else 0), "polydet_plan")
+        flags = FLAG_FULL_GRID if full_grid else 0
+        if det_degs is None:
+            _check(L.polydet_plan(ctypes.byref(h), int(n), len(degs), d, int(nprimes), flags), "polydet_plan")
+        else:
+            D = (ctypes.c_int32 * len(degs))(*[int(x) for x in det_degs])
+            _check(L.polydet_plan_degrees(ctypes.byref(h), int(n), len(degs), d, D, int(nprimes), flags),
+                   "polydet_plan_degrees")
         self._h = h
+        self._query()
+
+    def _query(self) -> None:
+        L = lib()
+        h = self._h
         info = PlanInfo()
         _check(L.polydet_plan_query(h, ctypes.byref(info)), "polydet_plan_query")
         self.n, self.k, self.P, self.W = info.n, info.nvars, info.P, info.W
@@ -202,6 +274,8 @@ class Plan:
         self.full_grid = bool(info.flags & FLAG_FULL_GRID)
         self.eval_ws_words = int(info.eval_ws_words)
         self.interp_ws_words = int(info.interp_ws_words)
+        self.entries = int(info.entries)  # entries per prime of the evals tensor
+        self.items = self.entries - 1 if info.unique >= 0 else self.entries  # evaluated entries
         pr = (ctypes.c_uint32 * self.P)()
         _check(L.polydet_plan_primes(h, pr), "polydet_plan_primes")
         self.primes = list(pr)
@@ -213,6 +287,27 @@ class Plan:
             ex = (ctypes.c_int32 * max(1, self.M[v]))()
             _check(L.polydet_plan_nodes(h, v, ex), "polydet_plan_nodes")
             self.node_exps.append(list(ex[:self.M[v]]))
+
+    def set_entry_map(self, entry_map: np.ndarray, U: int) -> None:
+        """Evaluate only the U distinct entries (map [n*n], -1 = zero entry):
+        eval takes [U][E] coefficients and writes [prime][U + 1][G]."""
+        m = np.ascontiguousarray(entry_map, dtype=np.int32)
+        _check(lib().polydet_plan_set_entry_map(self._h, m.ctypes.data_as(_PI32), int(U)),
+               "polydet_plan_set_entry_map")
+        self._query()
+
+    def stream_ws_words(self, rows: int = 1) -> int:
+        """Workspace words eval_condense needs with slabs of ``rows`` nodes of x_1."""
+        return int(lib().polydet_stream_ws_words(self._h, int(rows)))
+
+    def eval_condense(self, coeffs: torch.Tensor, lo: int, hi: int, detvals: torch.Tensor,
+                      ws: torch.Tensor, stream=None) -> None:
+        """Evaluation and condensation streamed slab by slab through ``ws``."""
+        _check(lib().polydet_eval_condense(
+            self._h, _ptr(coeffs, torch.int32, self.items * self.E, "coeffs"), lo, hi,
+            _ptr(detvals, torch.int32, (hi - lo) * self.G, "detvals"),
+            _ptr(ws, torch.int32, 1, "workspace"), ctypes.c_uint64(ws.numel()), _stream(stream)),
+            "polydet_eval_condense")
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -246,16 +341,14 @@ class Plan:
 
     def eval(self, coeffs: torch.Tensor, lo: int, hi: int, evals: torch.Tensor,
              ws: Optional[torch.Tensor] = None, stream=None) -> None:
-        n2 = self.n * self.n
-        _check(lib().polydet_eval(self._h, _ptr(coeffs, torch.int32, n2 * self.E, "coeffs"), lo, hi,
-                                  _ptr(evals, torch.int32, (hi - lo) * n2 * self.G, "evals"),
+        _check(lib().polydet_eval(self._h, _ptr(coeffs, torch.int32, self.items * self.E, "coeffs"), lo, hi,
+                                  _ptr(evals, torch.int32, (hi - lo) * self.entries * self.G, "evals"),
                                   self._ws(ws, self.eval_ws_words, hi - lo, "polydet_eval"),
                                   _stream(stream)), "polydet_eval")
 
     def condense(self, evals: torch.Tensor, lo: int, hi: int, detvals: torch.Tensor, stream=None) -> None:
-        n2 = self.n * self.n
         _check(lib().polydet_condense_batch(
-            self._h, _ptr(evals, torch.int32, (hi - lo) * n2 * self.G, "evals"), lo, hi,
+            self._h, _ptr(evals, torch.int32, (hi - lo) * self.entries * self.G, "evals"), lo, hi,
             _ptr(detvals, torch.int32, (hi - lo) * self.G, "detvals"), _stream(stream)),
             "polydet_condense_batch")
 
@@ -448,14 +541,16 @@ def mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, we
                                   float(weight_decay), _stream(stream)), "polydet_mlp_adam")
 
 
-def probe_int_peaks(stream=None) -> tuple[float, float]:
-    """(32-bit multiply-adds per second, fused modular updates per second)
-    measured on the current device by the library's probe kernels."""
+def probe_int_peaks(stream=None) -> tuple[float, float, float]:
+    """(32-bit multiply-adds per second, single-step modular updates per
+    second, two-step element updates per second) measured on the current
+    device by the library's probe kernels."""
     a = ctypes.c_double(0)
     u = ctypes.c_double(0)
-    _check(lib().polydet_probe_int_peaks(_stream(stream), ctypes.byref(a), ctypes.byref(u)),
+    u3 = ctypes.c_double(0)
+    _check(lib().polydet_probe_int_peaks(_stream(stream), ctypes.byref(a), ctypes.byref(u), ctypes.byref(u3)),
            "polydet_probe_int_peaks")
-    return a.value, u.value
+    return a.value, u.value, u3.value
 
 
 def limbs_to_ints(limbs: np.ndarray, W: int) -> List[int]:

@@ -96,7 +96,7 @@ static void update_ws(polydet_batch_s *b) {
     if (b->mode[pl->n] == POLYDET_BATCH_FUSED) {
       if (pl->nvars > 1) need = std::max<uint64_t>(need, pd_partial_ws_words(pl) * (uint64_t)pl->P);
     } else {
-      need = std::max<uint64_t>(need, pd_head_ws_words(pl));
+      need = std::max<uint64_t>(need, pd_head_ws_words(pl) * (uint64_t)pl->P);
       cmax = std::max<uint64_t>(cmax, (uint64_t)chunk_primes(b, pl) * pl->n * pl->n *
                                           (uint64_t)pd_tail_layout(pl).entry);
     }
@@ -380,7 +380,7 @@ extern "C" int polydet_batch_eval_n(polydet_batch_t b, int n, const int32_t *coe
     cudaStream_t st = b->fan[j % kFan];
     uint32_t *scratch = ws + kWsHead + (uint64_t)(j % kFan) * b->scratch_stride;
     if (b->mode[pl->n] == POLYDET_BATCH_MATERIALIZED) {
-      rc = pd_eval_head(pl, coeffs + b->coeff_off[j], partial + b->part_off[j], scratch, st);
+      rc = pd_eval_head(pl, coeffs + b->coeff_off[j], 0, pl->P, partial + b->part_off[j], scratch, st);
       if (rc) return rc;
       continue;
     }
@@ -427,7 +427,7 @@ static int condense_materialized(polydet_batch_s *b, int n, const uint32_t *part
       const int buf = c & 1;
       uint32_t *chunk = ws + kWsHead + (uint64_t)buf * b->chunk_max;
       if (c >= 2) PD_CUDA(cudaStreamWaitEvent(sd, b->ev[2 + buf], 0));  // its last reader is done
-      int rc = pd_eval_tail(pl, partial + b->part_off[j], lo, hi, chunk, lay, sd);
+      int rc = pd_eval_tail(pl, partial + b->part_off[j], 0, lo, hi, 0, pl->M[0], chunk, lay, sd);
       if (rc) return rc;
       PD_CUDA(cudaEventRecord(b->ev[buf], sd));
       PD_CUDA(cudaStreamWaitEvent(st, b->ev[buf], 0));

@@ -69,6 +69,12 @@ struct polydet_plan_s {
   uint32_t *d_mfull;      // [W] M
   uint32_t *d_status;     // 1 word
   int status_shared;      // 1: d_status belongs to a batch (one word for all its jobs)
+  // entries: evaluated matrix entry e = i n + j of a node is entry ent[e] of
+  // the evals tensor, which holds nent entries per prime; nitems of them are
+  // evaluated from coefficients (all n^2 by default; with an entry map the U
+  // distinct ones, and entry U is the zero entry)
+  int ent[POLYDET_MAX_N * POLYDET_MAX_N];
+  int nent, nitems;
   uint64_t eval_ws_words;   // caller scratch per prime for polydet_eval
   uint64_t interp_ws_words; // caller scratch per prime for polydet_interp
   int tw_off[POLYDET_MAX_VARS];
@@ -114,6 +120,11 @@ struct EvLayout {
 };
 int pd_launch_condense(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay, int prime_lo,
                        int nprimes, uint32_t *detvals, cudaStream_t st);
+// The same over G nodes per prime (a slab of the grid), determinants of prime
+// slot q at detvals + q * det_stride.
+int pd_launch_condense_nodes(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay, int64_t G,
+                             int64_t det_stride, int prime_lo, int nprimes, uint32_t *detvals,
+                             cudaStream_t st);
 
 // Evaluation of every variable but the last (x_k), for the fused kernels:
 // out[q][row][entry][Lp] with row over prod_{v<k} M_v (lex) holding the
@@ -123,23 +134,28 @@ int pd_eval_partial(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int
                     uint32_t *out, int Lp, uint32_t *ws, cudaStream_t st);
 uint64_t pd_partial_ws_words(const polydet_plan_s *pl);
 
-// Evaluation in two parts, for the batched form's materialized classes.
-// Head: passes of x_k, ..., x_2 for all P primes into head[q][entry][S1]
-// with S1 = pd_head_words(pl) (x_1 still in coefficients: (d_1 + 1) rows of
-// prod_{v>1} M_v nodes); needs pd_head_ws_words(pl) words of scratch.  One
-// variable: the coefficients reduced mod p_q.
-// Tail: the x_1 pass of primes [lo, hi) from the head into
-// evals[q - lo][entry][G], the layout polydet_condense_batch reads.
+// Evaluation in two parts, for the batched form's materialized classes and
+// the streamed single-plan form.
+// Head: passes of x_k, ..., x_2 for primes [lo, hi) into
+// head[q - lo][item][S1] with S1 = pd_head_words(pl) (x_1 still in
+// coefficients: (d_1 + 1) rows of prod_{v>1} M_v nodes); needs
+// pd_head_ws_words(pl) words of scratch per prime.  One variable: the
+// coefficients reduced mod p_q.  Items are the plan's evaluated entries
+// (n^2, or the distinct ones of an entry map).
+// Tail: the x_1 pass of primes [lo, hi) from the head (whose slot 0 is prime
+// head_q0) into evals[q - lo][entry][rows][B'] for the x_1 nodes
+// [row_lo, row_hi), the layout the condensation kernel reads.
 uint64_t pd_head_words(const polydet_plan_s *pl);
 uint64_t pd_head_ws_words(const polydet_plan_s *pl);
-int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, uint32_t *head, uint32_t *ws,
-                 cudaStream_t st);
-int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int lo, int hi, uint32_t *evals,
-                 EvLayout lay, cudaStream_t st);
-// The tail's layout: rows of the first variable padded to 32 words when a
-// row holds at least 1024 nodes (aligned rows store at full bandwidth; on
-// shorter rows the padding would cost more read traffic than it saves).
-EvLayout pd_tail_layout(const polydet_plan_s *pl);
+int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int hi, uint32_t *head,
+                 uint32_t *ws, cudaStream_t st);
+int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int head_q0, int lo, int hi,
+                 int row_lo, int row_hi, uint32_t *evals, EvLayout lay, cudaStream_t st);
+// The tail's layout for `rows` nodes of x_1 (0: all M_1): rows of the other
+// variables' B nodes, padded to 32 words when a row holds at least 1024 nodes
+// (aligned rows store at full bandwidth; on shorter rows the padding would
+// cost more read traffic than it saves).
+EvLayout pd_tail_layout(const polydet_plan_s *pl, int rows = 0);
 
 // One (job, prime) pair of a fused launch: the nodes [0, G) of that job and
 // prime, cut into items of S consecutive nodes (S = threads / lanes per det).

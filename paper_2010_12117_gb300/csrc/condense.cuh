@@ -20,13 +20,15 @@
 // as prod_{c<n-1} Q_c with Q_c = prod_{j<=c} v_jj, and inverted once by
 // Fermat's little theorem at the end, instead of one inverse per step.
 //
-// Pivot search (Algorithm 3's first nonzero entry): when the pivot a_cc is
-// zero, the first row r > c with a_rc != 0 is added to row c, which leaves
-// the determinant unchanged.  If the column is zero below c the pivot stays 0
-// and the result is 0, as the paper states.  The elimination first runs
-// without any search (no warp vote per step); a zero pivot is only recorded,
-// and the rare warp that met one redoes its matrices with the search
-// (ElimStep, out of line).
+// The fast pass takes the steps two at a time (Fast2Step: the Schur
+// complement of the leading 2 x 2 block, one three-product sum and one REDC
+// per element and pair of steps) and runs without any search and without a
+// warp vote per step; a zero pivot (a zero 2 x 2 minor) is only recorded.
+// Pivot search (Algorithm 3's first nonzero entry), for the rare warp that
+// met one: the matrices are redone one step at a time (ElimStep, out of
+// line); when the pivot a_cc is zero, the first row r > c with a_rc != 0 is
+// added to row c, which leaves the determinant unchanged.  If the column is
+// zero below c the pivot stays 0 and the result is 0, as the paper states.
 #pragma once
 
 #include "common.cuh"
@@ -125,79 +127,114 @@ struct ElimStep<NN, T, NN> {
   static PD_D void run(uint32_t (&)[M][NN], int, uint32_t, uint32_t, uint32_t &, uint32_t &) {}
 };
 
-// The same elimination without the pivot search: no warp vote per step, so
-// the steps overlap freely (the vote is a convergence point on every step),
-// and without the per-column range test (see the update below).
-// A zero pivot is only recorded in `zero`; the caller then redoes the whole
-// matrix with ElimStep.  For matrices with nonzero leading minors - almost
-// every node of a random polynomial matrix mod a 31-bit prime - the result
-// is the one ElimStep computes.
+// Two elimination steps at once (columns c and c + 1), the form the fast
+// pass uses: with the trailing matrix's leading 2 x 2 block
+// [[a_cc, a_c,c+1], [a_c+1,c, a_c+1,c+1]] of determinant D2 and its Schur
+// complement S, for i, j >= c + 2
+//   D2 S_ij = D2 a_ij + C1_j a_ic + C2_j a_i,c+1,
+//   C1_j = a_c,c+1 a_c+1,j - a_c+1,c+1 a_cj,  C2_j = a_c+1,c a_cj - a_cc a_c+1,j,
+// and det(trailing) = D2 det(S) = det(D2 S) / D2^(m - 1) with m = n - c - 2
+// rows left.  Each element costs one three-product sum and one REDC
+// (mfms3) instead of the two products and two REDCs of two single steps;
+// C1_j and C2_j cost two REDCs per column and pair of steps.  The pivot
+// bookkeeping is ElimStep's with D2 as the pivot of a step that removes two
+// rows: den gains Q^2 (Q^1 for a single step) before Q gains the pivot, so
+// that every pivot ends up in den to the power of the rows left after its
+// step.  A zero D2 is only recorded (the caller redoes the matrix with
+// ElimStep); an odd order ends with one single step (the last 1 x 1 pivot).
+// Needs p <= PD_FOLD3_MAX.
 template <int NN, int T, int c>
-struct FastStep {
+struct Fast2Step {
   static constexpr int M = (NN + T - 1) / T;
-  static PD_D void run(uint32_t (&a)[M][NN], int t, uint32_t p, uint32_t pinv, uint32_t &Q,
+  static constexpr int S = ColLayout<NN, T>::S;
+  static PD_D uint32_t bcast(uint32_t v, int owner) {
+    return (T == 1) ? v : __shfl_sync(PD_FULL, v, owner, T);
+  }
+  static PD_D void run(uint32_t (&a)[M][NN], uint32_t p, uint32_t pinv, uint32_t &Q,
                        uint32_t &den, bool &zero) {
-    constexpr int owner = (c + ColLayout<NN, T>::S) % T;
-    constexpr int mc = (c + ColLayout<NN, T>::S) / T;
-    const uint32_t piv = (T == 1) ? a[mc][c] : __shfl_sync(PD_FULL, a[mc][c], owner, T);
-    zero |= (piv == 0u);
-    if (c < NN - 1) {
-      // row by row: one broadcast a_ic live at a time, beside the M values
-      // a_cj of this lane's columns (fewer live registers than all a_ic)
-#pragma unroll
-      for (int i = c + 1; i < NN; ++i) {
-        const uint32_t fi = (T == 1) ? a[mc][i] : __shfl_sync(PD_FULL, a[mc][i], owner, T);
+    constexpr int o0 = (c + S) % T, m0 = (c + S) / T;  // owner and slot of column c
+    if constexpr (c == NN - 1) {
+      const uint32_t piv = bcast(a[m0][c], o0);
+      zero |= (piv == 0u);
+      den = mmul(den, Q, p, pinv);
+      Q = mmul(Q, piv, p, pinv);
+    } else {
+      constexpr int o1 = (c + 1 + S) % T, m1 = (c + 1 + S) / T;  // column c + 1
+      const uint32_t a00 = bcast(a[m0][c], o0), a10 = bcast(a[m0][c + 1], o0);
+      const uint32_t a01 = bcast(a[m1][c], o1), a11 = bcast(a[m1][c + 1], o1);
+      const uint32_t d2 = mfms(a00, a11, a10, a01, p, pinv);
+      zero |= (d2 == 0u);
+      den = mmul(den, mmul(Q, Q, p, pinv), p, pinv);
+      Q = mmul(Q, d2, p, pinv);
+      if constexpr (c + 2 < NN) {
+        // every block that still holds a column j > c + 1 updates all its
+        // lanes, with no select: the other slots of a block that straddles
+        // c + 1 (columns <= c + 1, padding) are never read again, and blocks
+        // wholly left of c + 2 drop out at compile time
+        uint32_t c1[M], c2[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          // every block that still holds a column j > c updates all its
-          // lanes, with no select: in a block that straddles c, columns
-          // j < c and padding slots are never read again, and column c
-          // itself becomes a_cc a_ic - a_ic a_cc = 0 after its entries were
-          // broadcast; blocks wholly left of c drop out at compile time
-          constexpr int S = ColLayout<NN, T>::S;
-          if (T * m + T - 1 - S > c) a[m][i] = mfms(piv, a[m][i], fi, a[m][c], p, pinv);
+          if (T * m + T - 1 - S > c + 1) {
+            c1[m] = mfms(a01, a[m][c + 1], a11, a[m][c], p, pinv);
+            c2[m] = mfms(a10, a[m][c], a00, a[m][c + 1], p, pinv);
+          }
         }
+        // row by row: the two broadcast column entries of row i are read
+        // before any lane rewrites row i
+#pragma unroll
+        for (int i = c + 2; i < NN; ++i) {
+          const uint32_t bi = bcast(a[m0][i], o0), ei = bcast(a[m1][i], o1);
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            if (T * m + T - 1 - S > c + 1) a[m][i] = mfms3(d2, a[m][i], c1[m], bi, c2[m], ei, p, pinv);
+          }
+        }
+        Fast2Step<NN, T, c + 2>::run(a, p, pinv, Q, den, zero);
       }
-      Q = mmul(Q, piv, p, pinv);
-      den = mmul(den, Q, p, pinv);
-      FastStep<NN, T, c + 1>::run(a, t, p, pinv, Q, den, zero);
-    } else {
-      Q = mmul(Q, piv, p, pinv);
     }
   }
 };
 
-template <int NN, int T>
-struct FastStep<NN, T, NN> {
-  static constexpr int M = (NN + T - 1) / T;
-  static PD_D void run(uint32_t (&)[M][NN], int, uint32_t, uint32_t, uint32_t &, uint32_t &, bool &) {}
+// Words from a node's value of its first evals entry to its value of entry
+// (i, j), for every (i, j): e * (words per entry) normally; with an entry map
+// (repeated and zero entries) the slot of (i, j) times the same.  Passed by
+// value as a kernel parameter (compile-time indices after unrolling: the
+// loads take their offsets from the constant bank).
+template <int NN>
+struct EntryOff {
+  int64_t o[NN * NN];
 };
 
 // The pivoting elimination of one matrix read again from `base` (entry
-// (i, j) at base[(i NN + j) stride]).  Kept out of line so that the rare
-// redo does not add to the register pressure of the fast pass.
+// (i, j) at base[off[i NN + j]]).  Kept out of line so that the rare redo
+// does not add to the register pressure of the fast pass.
 template <int NN, int T>
-__device__ __noinline__ uint2 elim_search(const uint32_t *base, int64_t stride, int t, ModP md) {
+__device__ __noinline__ uint2 elim_search(const uint32_t *base, const int64_t *off, int t, ModP md) {
   constexpr int M = (NN + T - 1) / T;
   uint32_t a[M][NN];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const int j = col_of<NN, T>(t, m);
 #pragma unroll
-    for (int i = 0; i < NN; ++i) a[m][i] = (j >= 0) ? base[(int64_t)(i * NN + j) * stride] : 0u;
+    for (int i = 0; i < NN; ++i) a[m][i] = (j >= 0) ? base[off[i * NN + j]] : 0u;
   }
   uint32_t Q = md.r1, den = md.r1;
   ElimStep<NN, T, 0>::run(a, t, md.p, md.pinv, Q, den);
   return make_uint2(Q, den);
 }
 
+// G nodes per prime (node g of prime slot q: entry (i, j) at
+// evals[q prime_words + (g / rowlen) rowstride + g % rowlen + off[i n + j]]);
+// determinant of node g of prime slot q to detvals[q det_stride + g].
 template <int NN, int T, int MINB>
 __global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__restrict__ evals,
                                                        uint32_t *__restrict__ detvals, int64_t G,
-                                                       EvLayout lay,
+                                                       int64_t det_stride, EvLayout lay,
+                                                       int64_t prime_words,
                                                        const ModP *__restrict__ mod,
                                                        const uint32_t *__restrict__ rn,
-                                                       int prime_lo) {
+                                                       int prime_lo,
+                                                       const __grid_constant__ EntryOff<NN> off) {
   constexpr int M = (NN + T - 1) / T;
   const int qrel = blockIdx.y;
   const int q = prime_lo + qrel;
@@ -208,22 +245,26 @@ __global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__r
   const bool active = g < G;
   const int64_t gg = active ? g : (G - 1);
   const int64_t row = gg / lay.rowlen;
-  const int64_t Gs = lay.entry;  // stride between the entries of one node
-  const uint32_t *base = evals + (int64_t)qrel * NN * NN * Gs + row * lay.rowstride + (gg - row * lay.rowlen);
+  const uint32_t *base = evals + (int64_t)qrel * prime_words + row * lay.rowstride + (gg - row * lay.rowlen);
 
   uint32_t a[M][NN];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const int j = col_of<NN, T>(t, m);
 #pragma unroll
-    for (int i = 0; i < NN; ++i) a[m][i] = (j >= 0) ? __ldg(base + (int64_t)(i * NN + j) * Gs) : 0u;
+    for (int i = 0; i < NN; ++i) a[m][i] = (j >= 0) ? __ldg(base + off.o[i * NN + j]) : 0u;
   }
 
   uint32_t Q = md.r1, den = md.r1;
   bool zero = false;
-  FastStep<NN, T, 0>::run(a, t, p, pinv, Q, den, zero);
+  Fast2Step<NN, T, 0>::run(a, p, pinv, Q, den, zero);
+  // primes above PD_FOLD3_MAX (only plans of more than 67 primes reach them)
+  // redo every matrix with the pivoting elimination (the fast pass is not
+  // skipped: a branch around it costs the common case its register
+  // allocation)
+  zero |= p > PD_FOLD3_MAX;
   if (__any_sync(PD_FULL, zero)) {  // some matrix of this warp met a zero pivot
-    const uint2 qd = elim_search<NN, T>(base, Gs, t, md);
+    const uint2 qd = elim_search<NN, T>(base, off.o, t, md);
     Q = qd.x;
     den = qd.y;
   }
@@ -240,7 +281,8 @@ __global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__r
   __syncthreads();
   if ((int)threadIdx.x < S) {
     const int64_t gd = (int64_t)blockIdx.x * S + threadIdx.x;
-    if (gd < G) detvals[(int64_t)qrel * G + gd] = finish_det(fin_q[threadIdx.x], fin_d[threadIdx.x], md, rn[q]);
+    if (gd < G)
+      detvals[(int64_t)qrel * det_stride + gd] = finish_det(fin_q[threadIdx.x], fin_d[threadIdx.x], md, rn[q]);
   }
   (void)active;
 }
@@ -253,17 +295,21 @@ struct TeamFor {
 
 template <int NN, int HI>
 static int condense_dispatch(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay,
-                             int prime_lo, int nprimes, uint32_t *detvals, cudaStream_t st) {
+                             int64_t G, int64_t det_stride, int prime_lo, int nprimes,
+                             uint32_t *detvals, cudaStream_t st) {
   if (pl->n == NN) {
     constexpr int T = TeamFor<NN>::value;
     const int threads = 128;
     const int64_t teams_per_cta = threads / T;
-    dim3 grid((unsigned)((pl->G + teams_per_cta - 1) / teams_per_cta), (unsigned)nprimes);
-    condense_kernel<NN, T, TeamFor<NN>::minb><<<grid, threads, 0, st>>>(evals, detvals, pl->G, lay,
-                                                                        pl->d_mod, pl->d_rn, prime_lo);
+    EntryOff<NN> off;
+    for (int e = 0; e < NN * NN; ++e) off.o[e] = (int64_t)pl->ent[e] * lay.entry;
+    dim3 grid((unsigned)((G + teams_per_cta - 1) / teams_per_cta), (unsigned)nprimes);
+    condense_kernel<NN, T, TeamFor<NN>::minb><<<grid, threads, 0, st>>>(
+        evals, detvals, G, det_stride, lay, (int64_t)pl->nent * lay.entry, pl->d_mod, pl->d_rn, prime_lo, off);
     PD_CUDA(cudaGetLastError());
     return POLYDET_OK;
   }
-  if constexpr (NN < HI) return condense_dispatch<NN + 1, HI>(pl, evals, lay, prime_lo, nprimes, detvals, st);
+  if constexpr (NN < HI)
+    return condense_dispatch<NN + 1, HI>(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
   return POLYDET_EINVAL;
 }

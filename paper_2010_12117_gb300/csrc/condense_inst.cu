@@ -7,7 +7,7 @@
 #define PD_CAT(a, b) PD_CAT2(a, b)
 
 int PD_CAT(pd_condense_from_, PD_N_LO)(const polydet_plan_s *pl, const uint32_t *evals,
-                                       EvLayout lay, int prime_lo, int nprimes, uint32_t *detvals,
-                                       cudaStream_t st) {
-  return condense_dispatch<PD_N_LO, PD_N_HI>(pl, evals, lay, prime_lo, nprimes, detvals, st);
+                                       EvLayout lay, int64_t G, int64_t det_stride, int prime_lo,
+                                       int nprimes, uint32_t *detvals, cudaStream_t st) {
+  return condense_dispatch<PD_N_LO, PD_N_HI>(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
 }

@@ -29,7 +29,7 @@
 //     two products (2 p^2 < p 2^32), into its own slice of shared memory
 //     (rolled loops: small code, no register pressure);
 //  2. the slice is loaded into the register-resident matrix and goes through
-//     the elimination of condense_kernel (Algorithm 3).
+//     the two-step elimination of condense_kernel (Algorithm 3).
 #pragma once
 
 #include "bulk.cuh"
@@ -127,7 +127,8 @@ __device__ __noinline__ uint2 fused_det(const uint32_t *mine, int bd, int t, Mod
   }
   uint32_t Q = md.r1, den = md.r1;
   bool zero = false;
-  FastStep<NN, T, 0>::run(a, t, p, pinv, Q, den, zero);
+  Fast2Step<NN, T, 0>::run(a, p, pinv, Q, den, zero);
+  zero |= p > PD_FOLD3_MAX;  // as in condense_kernel: larger primes redo every matrix
   if (__any_sync(PD_FULL, zero))  // a zero pivot in this warp: redo with the search
     return fused_det_search<NN, T>(mine, bd, t, md);
   return make_uint2(Q, den);

@@ -49,7 +49,15 @@ struct TxArgs {
   // (item, column, coset group) triples, so that short rows still fill whole
   // CTAs; each column's cosets are cut into flat_groups consecutive groups
   int flat_items, flat_groups;
+  // forward passes: only output rows [row_lo, row_hi) are stored, as rows
+  // 0 .. row_hi - row_lo of the output (row_hi = 0: all Lout rows).  The
+  // register-direct kernel takes a window only in coset order, with row_lo
+  // a multiple of the coset size
+  int row_lo, row_hi;
 };
+
+// Output rows one column of a pass stores.
+PD_HD int out_rows(const TxArgs &a) { return a.row_hi ? a.row_hi - a.row_lo : a.Lout; }
 
 __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
   extern __shared__ uint32_t sm[];
@@ -123,7 +131,8 @@ __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
     const int L = a.olp > 1 ? a.olp : 1;
     const int J = N / L;
     const int rk = (r % J) * L + r / J;
-    if (rk < a.Lout) {
+    const int rlo = a.row_lo, rhi = a.row_hi ? a.row_hi : a.Lout;
+    if (rk >= rlo && rk < rhi) {
       if (a.inverse) v = mmul(scale, v, md.p, md.pinv);
       const int64_t aa = col / a.B, bb = col - aa * a.B;
       if (a.il_L) {
@@ -132,9 +141,9 @@ __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
               bb % a.il_L] = v;
       } else {
         const int64_t orow = a.out_row ? a.out_row : a.B;
-        a.out[out_base + (aa * a.Lout + rk) * orow + bb] = v;
+        a.out[out_base + (aa * (rhi - rlo) + rk - rlo) * orow + bb] = v;
       }
-    } else if (a.inverse && v != 0u) {
+    } else if (a.inverse && rk >= a.Lout && v != 0u) {
       bad = true;
     }
   }
@@ -237,7 +246,7 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
               bb % a.il_L;
     else
       obase = (int64_t)blockIdx.z * a.out_prime_stride + item * a.out_item_stride +
-              aa * a.Lout * ostride + bb;
+              aa * out_rows(a) * ostride + bb;
     op[k] = ok ? a.out + obase : nullptr;
   }
   const uint32_t *tw = a.tw + (size_t)q * a.tw_len + a.tw_off;
@@ -250,25 +259,30 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
   }
   // Natural order (olp <= 1): coset j holds rows j + J t, stored while
   // j < lim[t].  Coset order (olp == LP): coset j holds rows j LP + t, so
-  // only the first ceil(Lout / LP) cosets are computed.
+  // only the cosets of the stored rows are computed: those of
+  // [row_lo, row_hi) (row_lo a multiple of LP), whose first one lands in
+  // output row 0.
   const bool coset_rows = a.olp > 1;
-  const int Jc = coset_rows ? (a.Lout + LP - 1) / LP : J;
+  const int rhi = a.row_hi ? a.row_hi : a.Lout;
+  const int jbeg = coset_rows ? a.row_lo / LP : 0;
+  const int jend = coset_rows ? (rhi + LP - 1) / LP : J;
   int lim[LP];
   int64_t toff[LP];  // words from a coset's first row to its row t
 #pragma unroll
   for (int t = 0; t < LP; ++t) {
-    lim[t] = coset_rows ? a.Lout - t : a.Lout - J * t;
+    lim[t] = coset_rows ? rhi - t : a.Lout - J * t;
     toff[t] = (int64_t)(coset_rows ? t : J * t) * ostride;
   }
   const int64_t jstep = (int64_t)(coset_rows ? LP : 1) * ostride;  // next coset's first row
-  int jlo = 0, jhi = Jc;  // this thread's cosets
+  int jlo = jbeg, jhi = jend;  // this thread's cosets
   if (a.flat_items && a.flat_groups > 1) {
-    const int per = (Jc + a.flat_groups - 1) / a.flat_groups;
-    jlo = min(Jc, grp * per);
-    jhi = min(Jc, jlo + per);
+    const int nj = jend - jbeg;
+    const int per = (nj + a.flat_groups - 1) / a.flat_groups;
+    jlo = jbeg + min(nj, grp * per);
+    jhi = jbeg + min(nj, (jlo - jbeg) + per);
 #pragma unroll
     for (int k = 0; k < CPT; ++k)
-      if (op[k]) op[k] += jlo * jstep;
+      if (op[k]) op[k] += (jlo - jbeg) * jstep;
   }
   for (int j = jlo; j < jhi; ++j) {
     uint32_t w[LIN];
@@ -355,7 +369,8 @@ static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
   // rows of fewer than 8 columns (a job's first pass: B = 1) only with the
   // flattened grid below, and not into the interleaved partial layout
   const bool rows_ok = a.B >= 8 || (!a.il_L && ncols * items < ((int64_t)1 << 31) - 256);
-  if (!a.inverse && a.Lin <= 8 && rows_ok && (a.olp <= 1 || a.olp == lp_in)) {
+  const bool window_ok = a.row_hi == 0 || (a.olp > 1 && a.olp == lp_in && a.row_lo % lp_in == 0);
+  if (!a.inverse && a.Lin <= 8 && rows_ok && window_ok && (a.olp <= 1 || a.olp == lp_in)) {
     // columns per thread: more share each coset's twiddles, fewer leave
     // fewer idle lanes in the last CTA of a row of B columns
     const int cpt = a.B < 8 ? 1 : (ncols >= 8192 ? 4 : (ncols >= 2048 ? 2 : 1));
@@ -368,7 +383,8 @@ static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
     a.flat_groups = 1;
     if (a.flat_items) {
       const int J = a.N / lp_in;
-      const int Jc = (a.olp > 1) ? (a.Lout + lp_in - 1) / lp_in : J;
+      const int rhi = a.row_hi ? a.row_hi : a.Lout;
+      const int Jc = (a.olp > 1) ? (rhi + lp_in - 1) / lp_in - a.row_lo / lp_in : J;
       const int64_t base = ncols * items * nprimes;
       int64_t g = (152 * 1024 + base - 1) / base;
       g = std::min<int64_t>(g, Jc);
@@ -412,6 +428,13 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
   const int k = pl->nvars, np = hi - lo;
   const int64_t n2 = (int64_t)pl->n * pl->n;
   const uint64_t slot = n2 ? pl->eval_ws_words / (uint64_t)n2 : 0;
+  // with an entry map only the distinct entries are evaluated, and the zero
+  // entry's slot is cleared
+  const int64_t items = pl->nitems, nent = pl->nent;
+  if (nent > items)
+    PD_CUDA(cudaMemset2DAsync(evals + items * pl->G, (size_t)nent * pl->G * sizeof(uint32_t), 0,
+                              (size_t)(nent - items) * pl->G * sizeof(uint32_t), (size_t)np, st));
+  if (items == 0) return POLYDET_OK;
   const void *cur_in = coeffs;
   int64_t cur_item = pl->E, cur_prime = 0;
   int cur_i32 = 1;
@@ -433,11 +456,12 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
     if (v % 2 == 0) {  // even passes land in the output array (slot G per entry)
       a.out = evals;
       a.out_item_stride = pl->G;
+      a.out_prime_stride = nent * pl->G;
     } else {
       a.out = ws;
       a.out_item_stride = (int64_t)slot;
+      a.out_prime_stride = items * a.out_item_stride;
     }
-    a.out_prime_stride = n2 * a.out_item_stride;
     a.inverse = 0;
     a.prime_lo = lo;
     a.mod = pl->d_mod;
@@ -448,7 +472,7 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
     a.nvars = k;
     a.var = v;
     a.status = pl->d_status;
-    int rc = launch_pass(a, (int)n2, np, st);
+    int rc = launch_pass(a, (int)items, np, st);
     if (rc) return rc;
     cur_in = a.out;
     cur_item = a.out_item_stride;
@@ -756,12 +780,12 @@ uint64_t pd_head_ws_words(const polydet_plan_s *pl) {
   // passes v >= 2 with v even land in the scratch (so that v = 1 lands in head)
   uint64_t best = 0;
   for (int v = 2; v < pl->nvars; v += 2) best = std::max(best, words_after(pl, v - 1));
-  return best * (uint64_t)pl->n * pl->n * (uint64_t)pl->P;
+  return best * (uint64_t)pl->nitems;
 }
 
 __global__ void reduce_kernel(const int32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t len,
-                              const ModP *__restrict__ mod) {
-  const uint32_t p = mod[blockIdx.y].p;
+                              const ModP *__restrict__ mod, int lo) {
+  const uint32_t p = mod[lo + blockIdx.y].p;
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < len;
        f += (int64_t)gridDim.x * blockDim.x)
     out[(int64_t)blockIdx.y * len + f] = reduce_i32(in[f], p);
@@ -791,14 +815,16 @@ static TxArgs forward_pass(const polydet_plan_s *pl, int v, int lo) {
   return a;
 }
 
-int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, uint32_t *head, uint32_t *ws,
-                 cudaStream_t st) {
+int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, int lo, int hi, uint32_t *head,
+                 uint32_t *ws, cudaStream_t st) {
+  if (check_range(pl, lo, hi)) return POLYDET_EINVAL;
   const int k = pl->nvars;
-  const int64_t n2 = (int64_t)pl->n * pl->n;
+  const int64_t items = pl->nitems;
+  if (items == 0) return POLYDET_OK;
   if (k == 1) {
-    const int64_t len = n2 * pl->E;
+    const int64_t len = items * pl->E;
     const unsigned blocks = (unsigned)std::min<int64_t>((len + 255) / 256, 4096);
-    reduce_kernel<<<dim3(blocks, pl->P), 256, 0, st>>>(coeffs, head, len, pl->d_mod);
+    reduce_kernel<<<dim3(blocks, hi - lo), 256, 0, st>>>(coeffs, head, len, pl->d_mod, lo);
     PD_CUDA(cudaGetLastError());
     return POLYDET_OK;
   }
@@ -809,15 +835,15 @@ int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, uint32_t *head
   int64_t cur_item = pl->E, cur_prime = 0;
   int cur_i32 = 1;
   for (int v = k - 1; v >= 1; --v) {
-    TxArgs a = forward_pass(pl, v, 0);
+    TxArgs a = forward_pass(pl, v, lo);
     a.in = cur_in;
     a.in_item_stride = cur_item;
     a.in_prime_stride = cur_prime;
     a.in_is_i32 = cur_i32;
     a.out = (v % 2) ? head : ws;
     a.out_item_stride = (v % 2) ? S1 : S2;
-    a.out_prime_stride = n2 * a.out_item_stride;
-    int rc = launch_pass(a, (int)n2, pl->P, st);
+    a.out_prime_stride = items * a.out_item_stride;
+    int rc = launch_pass(a, (int)items, hi - lo, st);
     if (rc) return rc;
     cur_in = a.out;
     cur_item = a.out_item_stride;
@@ -827,28 +853,37 @@ int pd_eval_head(const polydet_plan_s *pl, const int32_t *coeffs, uint32_t *head
   return POLYDET_OK;
 }
 
-EvLayout pd_tail_layout(const polydet_plan_s *pl) {
+EvLayout pd_tail_layout(const polydet_plan_s *pl, int rows) {
   const int64_t B = pl->G / pl->M[0];  // nodes of the other variables: one row
   const int64_t Bs = B >= 1024 ? (B + 31) / 32 * 32 : B;  // padding <= 3 % of a row
-  return EvLayout{B, Bs, (int64_t)pl->M[0] * Bs};
+  return EvLayout{B, Bs, (int64_t)(rows > 0 ? rows : pl->M[0]) * Bs};
 }
 
-int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int lo, int hi, uint32_t *evals,
-                 EvLayout lay, cudaStream_t st) {
-  if (check_range(pl, lo, hi) || !head || !evals) return POLYDET_EINVAL;
-  const int64_t n2 = (int64_t)pl->n * pl->n;
+int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int head_q0, int lo, int hi,
+                 int row_lo, int row_hi, uint32_t *evals, EvLayout lay, cudaStream_t st) {
+  if (check_range(pl, lo, hi) || !head || !evals || lo < head_q0) return POLYDET_EINVAL;
+  const int64_t items = pl->nitems, nent = pl->nent;
   const int64_t S1 = (int64_t)pd_head_words(pl);
   TxArgs a = forward_pass(pl, 0, lo);
-  if (lay.rowlen != a.B || lay.entry != (int64_t)pl->M[0] * lay.rowstride) return POLYDET_EINVAL;
-  a.in = head + (int64_t)lo * n2 * S1;
+  if (row_lo < 0 || row_hi > pl->M[0] || row_lo >= row_hi) return POLYDET_EINVAL;
+  if (lay.rowlen != a.B || lay.entry != (int64_t)(row_hi - row_lo) * lay.rowstride) return POLYDET_EINVAL;
+  if (row_lo > 0 || row_hi < pl->M[0]) {
+    a.row_lo = row_lo;
+    a.row_hi = row_hi;
+  }
+  if (nent > items)  // the zero entry's slot (entry map)
+    PD_CUDA(cudaMemset2DAsync(evals + items * lay.entry, (size_t)nent * lay.entry * sizeof(uint32_t), 0,
+                              (size_t)(nent - items) * lay.entry * sizeof(uint32_t), (size_t)(hi - lo), st));
+  if (items == 0) return POLYDET_OK;
+  a.in = head + (int64_t)(lo - head_q0) * items * S1;
   a.in_item_stride = S1;
-  a.in_prime_stride = n2 * S1;
+  a.in_prime_stride = items * S1;
   a.in_is_i32 = 0;
   a.out = evals;
   a.out_row = lay.rowstride;
   a.out_item_stride = lay.entry;
-  a.out_prime_stride = n2 * lay.entry;
-  return launch_pass(a, (int)n2, hi - lo, st);
+  a.out_prime_stride = nent * lay.entry;
+  return launch_pass(a, (int)items, hi - lo, st);
 }
 
 uint64_t pd_partial_ws_words(const polydet_plan_s *pl) {
@@ -926,4 +961,53 @@ extern "C" int polydet_condense_batch(polydet_plan_t pl, const uint32_t *evals, 
   if (check_range(pl, lo, hi) || !evals || !detvals) return POLYDET_EINVAL;
   const EvLayout lay = {pl->G, pl->G, pl->G};
   return pd_launch_condense(pl, evals, lay, lo, hi - lo, detvals, (cudaStream_t)stream);
+}
+
+// Streamed evaluation + condensation (multi-round evaluation of Sec. 3.1):
+// the workspace holds one prime's head tensor (every variable but x_1
+// evaluated) and, after it, the head passes' scratch, which the slabs of
+// evaluated matrices reuse once the head is complete.
+static int stream_quantum(const polydet_plan_s *pl) {
+  return pl->full ? 1 : pl->LPo[0];  // slab starts on a coset of x_1 (node grid)
+}
+
+static uint64_t stream_head_words(const polydet_plan_s *pl) {
+  return ((uint64_t)pl->nitems * pd_head_words(pl) + 63) / 64 * 64;
+}
+
+extern "C" uint64_t polydet_stream_ws_words(polydet_plan_t pl, int rows) {
+  if (!pl || rows < 1) return 0;
+  const int qn = stream_quantum(pl);
+  rows = std::min(pl->M[0], (rows + qn - 1) / qn * qn);
+  const uint64_t slab = (uint64_t)pl->nent * (uint64_t)pd_tail_layout(pl, rows).entry;
+  return stream_head_words(pl) + std::max<uint64_t>(pd_head_ws_words(pl), slab);
+}
+
+extern "C" int polydet_eval_condense(polydet_plan_t pl, const int32_t *coeffs, int lo, int hi,
+                                     uint32_t *detvals, uint32_t *ws, uint64_t ws_words, void *stream) {
+  if (check_range(pl, lo, hi) || !coeffs || !detvals || !ws) return POLYDET_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int qn = stream_quantum(pl), M0 = pl->M[0];
+  const uint64_t hw = stream_head_words(pl);
+  if (ws_words < polydet_stream_ws_words(pl, 1)) return POLYDET_EINVAL;
+  // slab rows: as many as the workspace holds, a multiple of the coset size
+  const uint64_t row_words = (uint64_t)pl->nent * (uint64_t)pd_tail_layout(pl, 1).entry;
+  int R = (int)std::min<uint64_t>((uint64_t)M0, (ws_words - hw) / std::max<uint64_t>(row_words, 1));
+  if (R < M0) R = std::max(qn, R / qn * qn);
+  uint32_t *head = ws, *rest = ws + hw;
+  const int64_t B = pl->G / M0;
+  for (int q = lo; q < hi; ++q) {
+    int rc = pd_eval_head(pl, coeffs, q, q + 1, head, rest, st);
+    if (rc) return rc;
+    for (int r0 = 0; r0 < M0; r0 += R) {
+      const int r1 = std::min(M0, r0 + R);
+      const EvLayout lay = pd_tail_layout(pl, r1 - r0);
+      rc = pd_eval_tail(pl, head, q, q, q + 1, r0, r1, rest, lay, st);
+      if (rc) return rc;
+      rc = pd_launch_condense_nodes(pl, rest, lay, (int64_t)(r1 - r0) * B, pl->G, q, 1,
+                                    detvals + (int64_t)(q - lo) * pl->G + (int64_t)r0 * B, st);
+      if (rc) return rc;
+    }
+  }
+  return POLYDET_OK;
 }

@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -22,7 +23,10 @@ void pd_set_error(const char *what, cudaError_t e) {
 extern "C" const char *polydet_last_error(void) { return g_err; }
 
 // ---------------------------------------------------------------------------
-// Prime table: p = c * 2^20 + 1 in (2^30, 2^31), largest first.  Primality by
+// Prime table: p = c * 2^20 + 1 in (2^30, 2^31): the 67 primes up to
+// PD_FOLD3_MAX first, largest first, then the 24 above it, largest first (the
+// condensation's two-step elimination needs p <= PD_FOLD3_MAX, so every
+// plan of up to 67 primes runs it on all of them).  Primality by
 // Miller-Rabin with bases 2, 7, 61 (deterministic below 4,759,123,141).
 // ---------------------------------------------------------------------------
 static bool is_prime_u32(uint32_t n) {
@@ -54,9 +58,12 @@ static bool is_prime_u32(uint32_t n) {
 static const std::vector<uint32_t> &prime_table() {
   static std::vector<uint32_t> t;
   if (t.empty()) {
-    for (uint32_t c = (0x7fffffffu >> 20); c > (0x40000000u >> 20); --c) {
-      uint32_t p = (c << 20) + 1u;
-      if (p > 0x40000000u && p < 0x80000000u && is_prime_u32(p)) t.push_back(p);
+    for (int above = 0; above < 2; ++above) {
+      for (uint32_t c = (0x7fffffffu >> 20); c > (0x40000000u >> 20); --c) {
+        uint32_t p = (c << 20) + 1u;
+        if ((p > PD_FOLD3_MAX) == (above == 1) && p > 0x40000000u && p < 0x80000000u && is_prime_u32(p))
+          t.push_back(p);
+      }
     }
   }
   return t;
@@ -123,6 +130,90 @@ extern "C" int polydet_hadamard_primes(int n, const int64_t *entry_l1, int *npri
   if (!P) return POLYDET_EPRIMES;
   *nprimes_out = P;
   if (log2_bound_out) *log2_bound_out = (double)lb;
+  return POLYDET_OK;
+}
+
+// Largest weight of a perfect matching of the n x n weights w (row-major;
+// forbidden pairs marked by ok[i * n + j] == 0), by the Hungarian method with
+// potentials on costs -w (O(n^3)); -1 when every perfect matching uses a
+// forbidden pair.
+static int64_t max_matching(int n, const std::vector<int64_t> &w, const std::vector<char> &ok) {
+  const int64_t INF = (int64_t)1 << 50, FORBID = (int64_t)1 << 40;
+  std::vector<int64_t> u(n + 1, 0), v(n + 1, 0), way(n + 1, 0), minv(n + 1);
+  std::vector<int> pcol(n + 1, 0);  // pcol[j] = row matched to column j (1-based)
+  std::vector<char> used(n + 1);
+  auto cost = [&](int i, int j) { return ok[(size_t)i * n + j] ? -w[(size_t)i * n + j] : FORBID; };
+  for (int i = 1; i <= n; ++i) {
+    pcol[0] = i;
+    int j0 = 0;
+    std::fill(minv.begin(), minv.end(), INF);
+    std::fill(used.begin(), used.end(), 0);
+    do {
+      used[j0] = 1;
+      const int i0 = pcol[j0];
+      int64_t delta = INF;
+      int j1 = 0;
+      for (int j = 1; j <= n; ++j) {
+        if (used[j]) continue;
+        const int64_t cur = cost(i0 - 1, j - 1) - u[i0] - v[j];
+        if (cur < minv[j]) {
+          minv[j] = cur;
+          way[j] = j0;
+        }
+        if (minv[j] < delta) {
+          delta = minv[j];
+          j1 = j;
+        }
+      }
+      for (int j = 0; j <= n; ++j) {
+        if (used[j]) {
+          u[pcol[j]] += delta;
+          v[j] -= delta;
+        } else {
+          minv[j] -= delta;
+        }
+      }
+      j0 = j1;
+    } while (pcol[j0] != 0);
+    do {
+      const int j1 = (int)way[j0];
+      pcol[j0] = pcol[j1];
+      j0 = j1;
+    } while (j0);
+  }
+  int64_t tot = 0;
+  for (int j = 1; j <= n; ++j) {
+    const int i = pcol[j] - 1;
+    if (!ok[(size_t)i * n + (j - 1)]) return -1;
+    tot += w[(size_t)i * n + (j - 1)];
+  }
+  return tot;
+}
+
+extern "C" int polydet_det_degree_bound(int n, int nvars, const int32_t *entry_degs, int32_t *D_out) {
+  if (n < 1 || n > POLYDET_MAX_N || nvars < 1 || nvars > POLYDET_MAX_VARS || !entry_degs || !D_out)
+    return POLYDET_EINVAL;
+  const size_t nn = (size_t)n * n;
+  std::vector<char> ok(nn);
+  for (size_t e = 0; e < nn; ++e) {
+    bool zero = true, bad = false;
+    for (int v = 0; v < nvars; ++v) {
+      const int32_t d = entry_degs[e * nvars + v];
+      if (d >= 0) zero = false;
+      if (d < -1) bad = true;
+    }
+    // an entry is either zero (-1 in every variable) or has a degree in each
+    for (int v = 0; v < nvars && !zero; ++v)
+      if (entry_degs[e * nvars + v] < 0) bad = true;
+    if (bad) return POLYDET_EINVAL;
+    ok[e] = zero ? 0 : 1;
+  }
+  std::vector<int64_t> w(nn);
+  for (int v = 0; v < nvars; ++v) {
+    for (size_t e = 0; e < nn; ++e) w[e] = ok[e] ? entry_degs[e * nvars + v] : 0;
+    const int64_t best = max_matching(n, w, ok);
+    D_out[v] = best < 0 ? 0 : (int32_t)best;
+  }
   return POLYDET_OK;
 }
 
@@ -270,8 +361,8 @@ static int upload(T **dst, const std::vector<T> &src) {
   return POLYDET_OK;
 }
 
-extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
-                            int nprimes, uint32_t flags) {
+static int plan_impl(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
+                     const int32_t *det_deg, int nprimes, uint32_t flags) {
   if (!out || n < 1 || n > POLYDET_MAX_N || nvars < 1 || nvars > POLYDET_MAX_VARS ||
       !entry_deg || (flags & ~POLYDET_FLAG_FULL_GRID))
     return POLYDET_EINVAL;
@@ -294,8 +385,14 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
       return POLYDET_EINVAL;
     }
     pl->d[v] = entry_deg[v];
-    pl->D[v] = n * entry_deg[v];
-    int64_t need = (int64_t)pl->D[v] + 1;
+    pl->D[v] = det_deg ? det_deg[v] : n * entry_deg[v];
+    if (pl->D[v] < 0 || (int64_t)pl->D[v] > (int64_t)n * entry_deg[v]) {
+      delete pl;
+      return POLYDET_EINVAL;
+    }
+    // D_v + 1 nodes for the interpolation, and at least d_v + 1 points in
+    // the transform so that an entry's d_v + 1 coefficients are not aliased
+    int64_t need = std::max<int64_t>((int64_t)pl->D[v] + 1, (int64_t)pl->d[v] + 1);
     if (need > POLYDET_MAX_GRID_DIM) {
       delete pl;
       return POLYDET_EDEGREE;
@@ -460,7 +557,85 @@ extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t
     free_plan(pl);
     return rc;
   }
+  for (int e = 0; e < n * n; ++e) pl->ent[e] = e;
+  pl->nent = n * n;
+  pl->nitems = n * n;
   *out = pl;
+  return POLYDET_OK;
+}
+
+extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
+                            int nprimes, uint32_t flags) {
+  return plan_impl(out, n, nvars, entry_deg, nullptr, nprimes, flags);
+}
+
+extern "C" int polydet_plan_degrees(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
+                                    const int32_t *det_deg, int nprimes, uint32_t flags) {
+  if (!det_deg) return POLYDET_EINVAL;
+  return plan_impl(out, n, nvars, entry_deg, det_deg, nprimes, flags);
+}
+
+extern "C" int polydet_plan_set_entry_map(polydet_plan_t pl, const int32_t *map, int U) {
+  if (!pl || !map || U < 0 || U > pl->n * pl->n) return POLYDET_EINVAL;
+  const int n2 = pl->n * pl->n;
+  std::vector<char> seen(U > 0 ? U : 1, 0);
+  for (int e = 0; e < n2; ++e) {
+    if (map[e] < -1 || map[e] >= U) return POLYDET_EINVAL;
+    if (map[e] >= 0) seen[map[e]] = 1;
+  }
+  for (int u = 0; u < U; ++u)
+    if (!seen[u]) return POLYDET_EINVAL;  // every distinct entry is used somewhere
+  for (int e = 0; e < n2; ++e) pl->ent[e] = map[e] < 0 ? U : map[e];
+  pl->nitems = U;
+  pl->nent = U + 1;  // slot U holds the zero entry
+  return POLYDET_OK;
+}
+
+// FNV-1a over an entry's coefficient words (the hash only groups candidates;
+// equality is decided by comparing the words).
+static uint64_t hash_words(const int32_t *x, int64_t len) {
+  uint64_t h = 1469598103934665603ull;
+  for (int64_t i = 0; i < len; ++i) {
+    uint32_t w = (uint32_t)x[i];
+    for (int b = 0; b < 4; ++b) {
+      h ^= (w >> (8 * b)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  }
+  return h;
+}
+
+extern "C" int polydet_unique_entries(int n, int64_t E, const int32_t *coeffs, int32_t *map_out,
+                                      int32_t *U_out, int32_t *unique_out) {
+  if (n < 1 || n > POLYDET_MAX_N || E < 1 || !coeffs || !map_out || !U_out) return POLYDET_EINVAL;
+  std::map<uint64_t, std::vector<int>> buckets;  // hash -> distinct entries (indices into firsts)
+  std::vector<int> firsts;                        // matrix entry where each distinct entry first occurs
+  for (int e = 0; e < n * n; ++e) {
+    const int32_t *c = coeffs + (int64_t)e * E;
+    bool zero = true;
+    for (int64_t i = 0; i < E && zero; ++i) zero = c[i] == 0;
+    if (zero) {
+      map_out[e] = -1;
+      continue;
+    }
+    auto &b = buckets[hash_words(c, E)];
+    int found = -1;
+    for (int u : b)
+      if (memcmp(coeffs + (int64_t)firsts[u] * E, c, (size_t)E * sizeof(int32_t)) == 0) {
+        found = u;
+        break;
+      }
+    if (found < 0) {
+      found = (int)firsts.size();
+      firsts.push_back(e);
+      b.push_back(found);
+    }
+    map_out[e] = found;
+  }
+  *U_out = (int32_t)firsts.size();
+  if (unique_out)
+    for (size_t u = 0; u < firsts.size(); ++u)
+      memcpy(unique_out + (int64_t)u * E, coeffs + (int64_t)firsts[u] * E, (size_t)E * sizeof(int32_t));
   return POLYDET_OK;
 }
 
@@ -489,6 +664,8 @@ extern "C" int polydet_plan_query(polydet_plan_t pl, polydet_plan_info *info) {
   info->flags = pl->full ? POLYDET_FLAG_FULL_GRID : 0u;
   info->eval_ws_words = pl->eval_ws_words;
   info->interp_ws_words = pl->interp_ws_words;
+  info->entries = pl->nent;
+  info->unique = (pl->nitems == pl->n * pl->n && pl->nent == pl->nitems) ? -1 : pl->nitems;
   return POLYDET_OK;
 }
 

@@ -1,10 +1,13 @@
 // Measurement utility: the integer-pipe ceilings that bound condensation.
 //
-// Two in-register streams with eight independent dependency chains per
+// Three in-register streams with eight independent dependency chains per
 // thread, enough warps per SM to hide latency, and no memory traffic:
 //  - plain 32-bit multiply-adds (x = x * x + c), the IMAD rate;
-//  - the condensation update r = (a*b - c*d) / R mod p (two 32x32->64
-//    multiply-adds, one REDC), the fused-update rate.
+//  - the single-step update r = (a*b - c*d) / R mod p (two 32x32->64
+//    multiply-adds, one REDC), the fused-update rate;
+//  - the two-step element update r = (a*b + c*d + e*f) / R mod p (three
+//    multiply-adds, one REDC; each stands for two single-step updates), the
+//    rate that bounds the condensation kernels' fast pass.
 // The rates bound the determinant kernels the way a copy bounds a memory
 // kernel.
 #include "common.cuh"
@@ -45,8 +48,30 @@ __global__ void __launch_bounds__(256) update_probe(uint32_t *out, int iters, ui
   if (s == 0x12345678u) out[tid] = s;
 }
 
-extern "C" int polydet_probe_int_peaks(void *stream, double *imad_per_s, double *update_per_s) {
-  if (!imad_per_s || !update_per_s) return POLYDET_EINVAL;
+__global__ void __launch_bounds__(256) pair_probe(uint32_t *out, int iters, uint32_t p,
+                                                  uint32_t pinv, uint32_t seed) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t a[8], b[8], e[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    a[j] = (seed + tid * 8u + j) % p;
+    b[j] = (seed * 3u + j * 7919u) % p;
+    e[j] = (seed * 5u + j * 104729u) % p;
+  }
+  const uint32_t d2 = (seed ^ 0x5bd1e995u) % p, c1 = (seed + 12345u) % p, c2 = (seed + 54321u) % p;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = mfms3(d2, a[j], c1, b[j], c2, e[j], p, pinv);
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s ^= a[j];
+  if (s == 0x12345678u) out[tid] = s;
+}
+
+extern "C" int polydet_probe_int_peaks(void *stream, double *imad_per_s, double *update_per_s,
+                                       double *pair_update_per_s) {
+  if (!imad_per_s || !update_per_s || !pair_update_per_s) return POLYDET_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0, sms = 0;
   PD_CUDA(cudaGetDevice(&dev));
@@ -77,6 +102,16 @@ extern "C" int polydet_probe_int_peaks(void *stream, double *imad_per_s, double 
   PD_CUDA(cudaEventSynchronize(e1));
   PD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   *update_per_s = (double)blocks * threads * (iters / 4) * 8.0 / (ms * 1e-3);
+  const uint32_t p3 = 1863319553u;  // a table prime <= PD_FOLD3_MAX, as mfms3 needs
+  uint32_t pinv3 = 1;
+  for (int i = 0; i < 5; ++i) pinv3 *= 2u - p3 * pinv3;
+  pair_probe<<<blocks, threads, 0, st>>>(out, iters / 4, p3, pinv3, 1u);
+  PD_CUDA(cudaEventRecord(e0, st));
+  pair_probe<<<blocks, threads, 0, st>>>(out, iters / 4, p3, pinv3, 2u);
+  PD_CUDA(cudaEventRecord(e1, st));
+  PD_CUDA(cudaEventSynchronize(e1));
+  PD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  *pair_update_per_s = (double)blocks * threads * (iters / 4) * 8.0 / (ms * 1e-3);
   PD_CUDA(cudaFreeAsync(out, st));
   PD_CUDA(cudaStreamSynchronize(st));
   cudaEventDestroy(e0);

@@ -15,17 +15,39 @@ from typing import List, Optional, Sequence
 import numpy as np
 import torch
 
-from .binding import EBOUND, Plan, PolydetError, as_u32, hadamard_primes, limbs_to_ints
+from .binding import (EBOUND, Plan, PolydetError, as_u32, det_degree_bound, entry_degrees,
+                      hadamard_primes, limbs_to_ints)
+from .binding import unique_entries as unique_entries_of
 from .resume import ResidueStore, input_digest
 
 
 @dataclass
 class DetResult:
-    coeffs: List[int]      # lex over the box prod [0, D_v]
+    coeffs: Optional[List[int]]  # lex over the box prod [0, D_v] (None: as_ints=False)
     D: tuple
     P: int
     W: int
     limbs: np.ndarray      # [C][W] uint32
+
+
+def unpermute_output(vals: Sequence[int], order: Sequence[int], box: Sequence[int]) -> List[int]:
+    """Output coefficients computed with the variables in ``order`` (lex over
+    ``box``, the extents D_v + 1 in that order) put back in the caller's
+    variable order: the inverse of the transposition ``permute_coeffs``
+    applies to the input."""
+    if list(order) == sorted(order):
+        return list(vals)
+    arr = np.empty(len(vals), dtype=object)
+    arr[:] = list(vals)
+    inv = [list(order).index(v) for v in range(len(order))]
+    return arr.reshape(tuple(int(b) for b in box)).transpose(inv).reshape(-1).tolist()
+
+
+def permute_coeffs(coeffs: np.ndarray, degs: Sequence[int], order: Sequence[int]) -> np.ndarray:
+    """[n][n][E] lex coefficients with the variables taken in ``order``."""
+    n = coeffs.shape[0]
+    t = np.asarray(coeffs).reshape((n, n) + tuple(int(d) + 1 for d in degs))
+    return t.transpose((0, 1) + tuple(2 + v for v in order)).reshape(n, n, -1)
 
 
 def entry_l1(coeffs: np.ndarray) -> np.ndarray:
@@ -38,40 +60,84 @@ def prime_count(coeffs: np.ndarray) -> int:
 
 
 def _chunk(plan: Plan, budget_bytes: int) -> int:
-    per_prime = 4 * (plan.n * plan.n * plan.G + plan.G + max(plan.eval_ws_words, plan.interp_ws_words))
+    per_prime = 4 * (plan.entries * plan.G + plan.G + max(plan.eval_ws_words, plan.interp_ws_words))
     return max(1, min(plan.P, budget_bytes // max(1, per_prime)))
 
 
 def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] = None,
                 store: Optional[ResidueStore] = None, budget_bytes: int = 8 << 30,
                 stream: Optional[torch.cuda.Stream] = None,
-                stop_after_chunks: Optional[int] = None, full_grid: bool = False) -> DetResult:
+                stop_after_chunks: Optional[int] = None, full_grid: bool = False,
+                tight_degrees: bool = False, unique_entries: bool = False,
+                streamed: Optional[bool] = None, as_ints: bool = True) -> DetResult:
     """Exact det of the polynomial matrix ``coeffs`` [n][n][E] (lex encoding
-    of Sec. 2) with entry degrees ``degs``; returns its coefficients."""
+    of Sec. 2) with entry degrees ``degs``; returns its coefficients over the
+    box prod [0, D_v].
+
+    ``tight_degrees``: D_v from the entries' degrees (the assignment bound of
+    polydet_det_degree_bound) instead of n d_v.  ``unique_entries``: evaluate
+    each distinct entry once (polydet_plan_set_entry_map).  ``streamed``:
+    evaluation and condensation slab by slab through a workspace within
+    ``budget_bytes`` (polydet_eval_condense), one prime at a time, with the
+    variable of lowest degree taken first (its nodes are the slabs); None
+    streams exactly when one prime's evaluated matrices exceed the budget.
+    ``as_ints``: False leaves ``coeffs`` None (outputs of hundreds of
+    millions of coefficients are read from ``limbs``)."""
     coeffs = np.asarray(coeffs)
     n = coeffs.shape[0]
     if coeffs.shape[:2] != (n, n):
         raise ValueError("coeffs must be [n][n][E]")
     if np.abs(coeffs).max(initial=0) >= 2 ** 31:
         raise ValueError("coefficients must fit in int32")
+    degs = tuple(int(d) for d in degs)
     P = nprimes if nprimes is not None else prime_count(coeffs)
-    plan = Plan(n, degs, P, full_grid=full_grid)
+    order = list(range(len(degs)))
+    if streamed is not False:
+        order = sorted(order, key=lambda v: (degs[v], v))
+    cp = permute_coeffs(coeffs, degs, order)
+    dp = tuple(degs[v] for v in order)
+    D = None
+    if tight_degrees:
+        D = det_degree_bound(entry_degrees(cp, dp), len(dp))
+    plan = Plan(n, dp, P, full_grid=full_grid, det_degs=D)
+    rows = np.ascontiguousarray(cp, dtype=np.int32).reshape(n * n, -1)
+    if unique_entries:
+        emap, U, uniq = unique_entries_of(cp)
+        plan.set_entry_map(emap, U)
+        rows = uniq
+    if streamed is None:
+        streamed = 4 * (plan.entries * plan.G + plan.G) > budget_bytes
+    if not streamed and order != sorted(order):  # the plain path keeps the caller's order
+        plan.close()
+        return determinant(coeffs, degs, nprimes=P, store=store, budget_bytes=budget_bytes,
+                           stream=stream, stop_after_chunks=stop_after_chunks, full_grid=full_grid,
+                           tight_degrees=tight_degrees, unique_entries=unique_entries, streamed=False,
+                           as_ints=as_ints)
     dev = torch.device("cuda")
     st = stream if stream is not None else torch.cuda.current_stream()
     with torch.cuda.stream(st):
-        c_dev = torch.from_numpy(np.ascontiguousarray(coeffs, dtype=np.int32).reshape(-1)).to(dev)
+        flat = np.ascontiguousarray(rows, dtype=np.int32).reshape(-1)
+        c_dev = torch.from_numpy(flat if flat.size else np.zeros(1, dtype=np.int32)).to(dev)
         residues = torch.empty(P * plan.C, dtype=torch.int32, device=dev)
         todo = list(range(P))
         if store is not None:
             store.open_job({"n": n, "degs": [int(d) for d in degs], "primes": plan.primes,
-                            "full_grid": bool(full_grid), "input": input_digest(coeffs, degs)})
+                            "full_grid": bool(full_grid), "input": input_digest(coeffs, degs),
+                            "det_degs": [int(x) for x in plan.D], "order": order})
             for q, r in store.done(P, plan.C).items():
                 residues[q * plan.C:(q + 1) * plan.C].copy_(torch.from_numpy(r.view(np.int32)))
                 todo.remove(q)
-        ch = _chunk(plan, budget_bytes)
-        evals = torch.empty(ch * n * n * plan.G, dtype=torch.int32, device=dev) if todo else None
+        if streamed:
+            ch = 1
+            ws_words = max(plan.stream_ws_words(1), plan.interp_ws_words,
+                           min(plan.stream_ws_words(plan.M[0]), max(0, budget_bytes // 4 - plan.G)))
+            evals = None
+            ws = torch.empty(ws_words, dtype=torch.int32, device=dev) if todo else None
+        else:
+            ch = _chunk(plan, budget_bytes)
+            evals = torch.empty(ch * plan.entries * plan.G, dtype=torch.int32, device=dev) if todo else None
+            ws = plan.workspace(ch) if todo else None
         detv = torch.empty(ch * plan.G, dtype=torch.int32, device=dev) if todo else None
-        ws = plan.workspace(ch) if todo else None
         runs: List[List[int]] = []  # consecutive primes, at most ch per launch
         for q in todo:
             if runs and runs[-1][1] == q and runs[-1][1] - runs[-1][0] < ch:
@@ -81,8 +147,11 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
         for done, (lo, hi) in enumerate(runs):
             if stop_after_chunks is not None and done >= stop_after_chunks:
                 raise InterruptedError("stopped after the requested number of chunks")
-            plan.eval(c_dev, lo, hi, evals, ws, st)
-            plan.condense(evals, lo, hi, detv, st)
+            if streamed:
+                plan.eval_condense(c_dev, lo, hi, detv, ws, st)
+            else:
+                plan.eval(c_dev, lo, hi, evals, ws, st)
+                plan.condense(evals, lo, hi, detv, st)
             plan.interp(detv, lo, hi, residues[lo * plan.C:hi * plan.C], ws, st)
             if store is not None:
                 # a restart point is only as good as its residues: read the
@@ -94,12 +163,23 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
                 host = as_u32(residues[lo * plan.C:hi * plan.C])
                 for q in range(lo, hi):
                     store.save(q, host[(q - lo) * plan.C:(q - lo + 1) * plan.C])
+        del evals, ws, detv
         limbs = torch.empty(plan.C * plan.W, dtype=torch.int32, device=dev)
         plan.crt(residues, limbs, st)
         status = plan.sync_status(st)
         if status:
             raise PolydetError(EBOUND, f"device status {status:#x}")
         host_limbs = as_u32(limbs).reshape(plan.C, plan.W)
-    out = DetResult(limbs_to_ints(host_limbs, plan.W), plan.D, plan.P, plan.W, host_limbs)
+    box = tuple(int(x) + 1 for x in plan.D)
+    vals = limbs_to_ints(host_limbs, plan.W) if as_ints else None
+    Dc = [0] * len(degs)
+    for i, v in enumerate(order):
+        Dc[v] = plan.D[i]
+    if order != sorted(order):
+        if as_ints:
+            vals = unpermute_output(vals, order, box)
+        inv = [order.index(v) for v in range(len(order))]
+        host_limbs = host_limbs.reshape(box + (plan.W,)).transpose(tuple(inv) + (len(order),)).reshape(-1, plan.W)
+    out = DetResult(vals, tuple(Dc), plan.P, plan.W, np.ascontiguousarray(host_limbs))
     plan.close()
     return out

@@ -18,7 +18,7 @@ import torch
 
 from .binding import (BATCH_FUSED, BATCH_MATERIALIZE_N, BATCH_MATERIALIZED, EBOUND, Plan,
                       PolydetError, as_u32, limbs_to_ints, tail_entry_words)
-from .pipeline import prime_count
+from .pipeline import permute_coeffs, prime_count, unpermute_output  # noqa: F401 (re-exported)
 
 
 class StageTimer:
@@ -179,26 +179,6 @@ def variable_order(n: int, degs: Sequence[int]) -> List[int]:
     in the first case and come out reversed in the second."""
     order = sorted(range(len(degs)), key=lambda v: (int(degs[v]), v))
     return order if n >= BATCH_MATERIALIZE_N else order[::-1]
-
-
-def unpermute_output(vals: Sequence[int], order: Sequence[int], box: Sequence[int]) -> List[int]:
-    """Output coefficients computed with the variables in ``order`` (lex over
-    ``box``, the extents D_v + 1 in that order) put back in the caller's
-    variable order: the inverse of the transposition ``permute_coeffs``
-    applies to the input."""
-    if list(order) == sorted(order):
-        return list(vals)
-    arr = np.empty(len(vals), dtype=object)
-    arr[:] = list(vals)
-    inv = [list(order).index(v) for v in range(len(order))]
-    return arr.reshape(tuple(int(b) for b in box)).transpose(inv).reshape(-1).tolist()
-
-
-def permute_coeffs(coeffs: np.ndarray, degs: Sequence[int], order: Sequence[int]) -> np.ndarray:
-    """[n][n][E] lex coefficients with the variables taken in ``order``."""
-    n = coeffs.shape[0]
-    t = np.asarray(coeffs).reshape((n, n) + tuple(int(d) + 1 for d in degs))
-    return t.transpose((0, 1) + tuple(2 + v for v in order)).reshape(n, n, -1)
 
 
 class BatchedRunner:

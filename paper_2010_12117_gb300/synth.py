@@ -15,6 +15,7 @@ Draw order (numpy ``default_rng(seed)``, PCG64), per workload:
 * ``dense_4x4``: one ``integers(-10, 11, (4, 4, 9))`` call.
 * ``sylvester_16``: f then g, each ``integers(-2**15, 2**15, (9, 7))`` indexed
   [power of y][power of x]; the 16x16 Sylvester matrix in y is then laid out.
+* ``sylvester`` / ``sylvester_15_four_vars``: see ``sylvester``.
 * ``sparse_12x12_xyz``: ``random((12, 12, 64)) < 0.3`` (monomial mask) then
   ``integers(-128, 128, (12, 12, 64))`` (values); masked-out values become 0.
 * ``batched``: per matrix, in order: n = integers(4, 25); k = integers(1, 4);
@@ -99,6 +100,56 @@ def sylvester_layout(f: np.ndarray, g: np.ndarray) -> PolyMatrix:
         for s in range(l + 1):
             c[l + r, r + s] = g[l - s]
     return PolyMatrix(n, (t - 1,), c)
+
+
+def sylvester(rng: np.random.Generator, m: int, l: int, degs_f: Sequence[int],
+              degs_g: Sequence[int], density: float, lo: int, hi: int) -> PolyMatrix:
+    """(m + l) x (m + l) Sylvester matrix in y of f = sum_{i<=m} f_i y^i and
+    g = sum_{i<=l} g_i y^i with f_i, g_i in Z[x1..xk] of degree <= degs_f
+    (degs_g) in x_v.  Draws, f's coefficients i = 0..m then g's: a monomial
+    mask ``random(E) < density`` and values ``integers(lo, hi, E)`` over the
+    polynomial's own degree box, then for each v with a positive degree the
+    pure power x_v^d_v gets ``integers(lo, hi)`` (1 where that draw is 0), so
+    that every f_i, g_i reaches its degree bound in every variable.  Entries
+    are encoded over the box of the larger bounds."""
+    degs_f = tuple(int(d) for d in degs_f)
+    degs_g = tuple(int(d) for d in degs_g)
+    box = tuple(max(a, b) for a, b in zip(degs_f, degs_g))
+
+    def draw(degs):
+        shape = tuple(d + 1 for d in degs)
+        E = int(np.prod(shape))
+        mask = rng.random(E) < density
+        vals = np.where(mask, rng.integers(lo, hi, E), 0).reshape(shape)
+        for v, d in enumerate(degs):
+            if d > 0:
+                idx = tuple(d if u == v else 0 for u in range(len(degs)))
+                x = int(rng.integers(lo, hi))
+                vals[idx] = x if x != 0 else 1
+        out = np.zeros(tuple(b + 1 for b in box), dtype=np.int64)
+        out[tuple(slice(0, d + 1) for d in degs)] = vals
+        return out.reshape(-1)
+
+    f = np.stack([draw(degs_f) for _ in range(m + 1)])
+    g = np.stack([draw(degs_g) for _ in range(l + 1)])
+    pm = sylvester_layout(f, g)
+    pm.degs = box
+    pm.name = f"sylvester_{m + l}_k{len(box)}"
+    pm.meta = {"m": m, "l": l, "degs_f": degs_f, "degs_g": degs_g}
+    return pm
+
+
+def sylvester_15_four_vars(seed: int, density: float = 0.01) -> PolyMatrix:
+    """15 x 15 Sylvester matrix in y of f (degree 8 in y) and g (degree 7)
+    over Z[x1, x2, x3, x4], coefficient polynomials of degree (22, 13, 9, 3)
+    for f and (18, 10, 7, 3) for g, int8 coefficients: its determinant (the
+    resultant) has degree at most 7 * 22 + 8 * 18 = 298, 171, 119 and 45 in
+    the four variables, the shape of the harmonic-elimination matrix of
+    Sec. 6 (whose polynomials the paper does not give)."""
+    rng = np.random.default_rng(seed)
+    pm = sylvester(rng, 8, 7, (22, 13, 9, 3), (18, 10, 7, 3), density, -128, 128)
+    pm.name = f"sylvester_15_x1x2x3x4/seed{seed}"
+    return pm
 
 
 def sylvester_16(seed: int) -> PolyMatrix:

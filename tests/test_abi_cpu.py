@@ -95,3 +95,69 @@ def test_team_sizes_are_usable_and_match_the_tuner():
         binding.team_size(0)
     with pytest.raises(binding.PolydetError):
         binding.team_size(33)
+
+
+def _rand_edeg(rng, n, k, dmax, pzero):
+    return [[None if rng.random() < pzero else tuple(int(x) for x in rng.integers(0, dmax + 1, k))
+             for _ in range(n)] for _ in range(n)]
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 6, 9, 13, 20, 32])
+def test_det_degree_bound_matches_oracle(n):
+    """The library's assignment bound (Hungarian method) against the oracle's
+    (brute force over permutations, or scipy's matching), with zero entries,
+    including matrices whose zeros leave no permutation (bound 0)."""
+    ensure_lib()
+    from paper_2010_12117_gb300 import binding
+    rng = np.random.default_rng(900 + n)
+    for pz in (0.0, 0.3, 0.7):
+        for _ in range(4):
+            e = _rand_edeg(rng, n, 3, 12, pz)
+            assert binding.det_degree_bound(e, 3) == oplan.assignment_degree_bound(e, 3), (n, pz)
+
+
+def test_det_degree_bound_of_the_four_variable_sylvester_target():
+    ensure_lib()
+    from paper_2010_12117_gb300 import binding, synth
+    pm = synth.sylvester_15_four_vars(0)
+    e = binding.entry_degrees(pm.coeffs, pm.degs)
+    assert binding.det_degree_bound(e) == (298, 171, 119, 45)
+    assert oplan.assignment_degree_bound(e, 4) == (298, 171, 119, 45)
+
+
+def test_unique_entries_against_an_independent_grouping():
+    """Entries with equal coefficient vectors share an index, in order of
+    first occurrence; zero entries map to -1; the distinct rows are the
+    first occurrences."""
+    ensure_lib()
+    from paper_2010_12117_gb300 import binding, synth
+    rng = np.random.default_rng(5)
+    cases = [synth.sylvester_16(1).coeffs, synth.random_matrix(rng, 7, (2, 1), 0.5, -3, 3).coeffs,
+             np.zeros((3, 3, 4), dtype=np.int64)]
+    base = rng.integers(-9, 9, (4, 6))
+    pick = rng.integers(0, 5, (6, 6))
+    c = np.zeros((6, 6, 6), dtype=np.int64)
+    for i in range(6):
+        for j in range(6):
+            c[i, j] = base[pick[i, j]] if pick[i, j] < 4 else 0
+    cases.append(c)
+    for coeffs in cases:
+        n, E = coeffs.shape[0], coeffs.shape[2]
+        m, U, uniq = binding.unique_entries(coeffs)
+        flat = coeffs.reshape(n * n, E)
+        seen = {}
+        want = []
+        for e in range(n * n):
+            key = tuple(int(x) for x in flat[e])
+            if not any(key):
+                want.append(-1)
+                continue
+            if key not in seen:
+                seen[key] = len(seen)
+            want.append(seen[key])
+        assert list(m) == want
+        assert U == len(seen)
+        for key, u in seen.items():
+            assert tuple(int(x) for x in uniq[u]) == key
+    m, U, _ = binding.unique_entries(synth.sylvester_16(1).coeffs)
+    assert U == 18  # f_0..f_8 and g_0..g_8

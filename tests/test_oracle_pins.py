@@ -274,8 +274,15 @@ PRIMES = modular.ntt_primes()
 
 def test_prime_table():
     assert len(PRIMES) == 91
-    assert PRIMES == sorted(PRIMES, reverse=True)
-    assert PRIMES[:3] == [2130706433, 2114977793, 2113929217]
+    low = [p for p in PRIMES if p <= modular.FOLD3_MAX]
+    assert len(low) == 67 and PRIMES[:67] == sorted(low, reverse=True)
+    assert PRIMES[67:] == sorted(PRIMES[67:], reverse=True) and min(PRIMES[67:]) > modular.FOLD3_MAX
+    assert PRIMES[:3] == [1863319553, 1835008001, 1811939329]
+    assert PRIMES[67:70] == [2130706433, 2114977793, 2113929217]
+    # FOLD3_MAX is the largest p for which floor(3 (p-1)^2 / 2^32) = r_max
+    # satisfies r_max + p < 2^32 and r_max < 2p
+    ok = lambda p: ((3 * (p - 1) ** 2) >> 32) + p <= 2 ** 32 - 1 and ((3 * (p - 1) ** 2) >> 32) < 2 * p
+    assert ok(modular.FOLD3_MAX) and not ok(modular.FOLD3_MAX + 1)
     for p in PRIMES:
         assert 2 ** 30 < p < 2 ** 31 and (p - 1) % (1 << 20) == 0
         assert sympy.isprime(p)
@@ -468,6 +475,65 @@ def test_certificate_catches_every_single_coefficient_error():
         assert not certificate.check(pm.coeffs.tolist(), pm.degs, tr, D, trials=2)
 
 
+def _rand_edeg(rng, n, k, dmax, pzero):
+    return [[None if rng.random() < pzero else tuple(int(x) for x in rng.integers(0, dmax + 1, k))
+             for _ in range(n)] for _ in range(n)]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7])
+def test_assignment_bound_brute_force_equals_matching(n):
+    rng = np.random.default_rng(70 + n)
+    for _ in range(20):
+        e = _rand_edeg(rng, n, 2, 9, 0.3)
+        assert plan.assignment_degree_bound(e, 2, brute=True) == plan.assignment_degree_bound(e, 2, brute=False)
+
+
+def test_assignment_bound_against_row_and_column_sums_and_closed_forms():
+    rng = np.random.default_rng(77)
+    for n in (3, 6, 9, 12):
+        e = _rand_edeg(rng, n, 3, 7, 0.2)
+        D = plan.assignment_degree_bound(e, 3)
+        for v in range(3):
+            rows = sum(max((x[v] for x in r if x is not None), default=0) for r in e)
+            cols = sum(max((e[i][j][v] for i in range(n) if e[i][j] is not None), default=0) for j in range(n))
+            assert D[v] <= min(rows, cols)
+    # upper triangular: only the identity avoids the zeros
+    e = [[(i + j, 1) if j >= i else None for j in range(6)] for i in range(6)]
+    assert plan.assignment_degree_bound(e, 2) == (sum(2 * i for i in range(6)), 6)
+    # a zero row: det = 0
+    e = [[(1,), (2,)], [None, None]]
+    assert plan.assignment_degree_bound(e, 1) == (0,)
+    # anti-diagonal degrees 0..9 and everything else of degree 0 except zeros
+    e = [[(9,) if i + j == 9 else None for j in range(10)] for i in range(10)]
+    assert plan.assignment_degree_bound(e, 1) == (90,)
+
+
+def test_assignment_bound_holds_and_is_attained():
+    """The bound holds for every determinant computed by O2, is attained by
+    generic dense matrices, and for Sylvester matrices equals the resultant
+    bound l deg f + m deg g."""
+    rng = np.random.default_rng(78)
+    for n, degs, dens in [(3, (2, 1), 0.5), (4, (1, 2), 0.3), (5, (2,), 0.4), (4, (1, 1, 1), 0.6)]:
+        for _ in range(3):
+            pm = rand_matrix(rng, n, degs, dens)
+            D = plan.assignment_degree_bound(plan.entry_degrees(pm.coeffs.tolist(), degs), len(degs))
+            box = plan.det_degree_bound(n, degs)
+            det = bareiss.det_packed(pm.coeffs.tolist(), degs)
+            arr = np.array(det, dtype=object).reshape([b + 1 for b in box])
+            for v in range(len(degs)):
+                nz = np.nonzero(np.array(arr != 0, dtype=bool))[v]
+                assert (nz.max() if len(nz) else 0) <= D[v]
+    pm = rand_matrix(rng, 4, (2, 3), 1.0)  # dense: generic, the bound is the degree
+    D = plan.assignment_degree_bound(plan.entry_degrees(pm.coeffs.tolist(), (2, 3)), 2)
+    assert D == (8, 12)
+    det = np.array(bareiss.det_packed(pm.coeffs.tolist(), (2, 3)), dtype=object).reshape(9, 13)
+    assert any(det[8, :]) and any(det[:, 12])
+    # Sylvester of f (deg_y 3, x-degree 2) and g (deg_y 2, x-degree 4): 2*2 + 3*4
+    s = synth.sylvester(rng, 3, 2, (2,), (4,), 0.9, -9, 10)
+    D = plan.assignment_degree_bound(plan.entry_degrees(s.coeffs.tolist(), s.degs), 1)
+    assert D == (2 * 2 + 3 * 4,)
+
+
 def test_workload_generators_shapes():
     a = synth.dense_4x4(0)
     assert a.coeffs.shape == (4, 4, 9) and a.coeffs.min() >= -10 and a.coeffs.max() <= 10
@@ -538,3 +604,42 @@ def test_gen_config_indices():
     assert len(s) == 20 and all(a.t < b.t for a, b in zip(s, s[1:]))
     with pytest.raises(ValueError):
         synth.gen_config(5, 1)
+
+
+def test_limbs_mod_q_against_python_integers():
+    """Residues of two's-complement limbs mod 2^31 - 1 equal those of the
+    Python integers they encode (negative, zero, extreme values)."""
+    rng = np.random.default_rng(41)
+    q = certificate.Q31
+    for W in (1, 2, 5, 11):
+        lim = 1 << (32 * W - 1)
+        xs = [0, -1, 1, lim - 1, -lim, q, -q] + [int(v) for v in rng.integers(-2 ** 62, 2 ** 62, 40)]
+        xs += [int.from_bytes(rng.bytes(4 * W), "little", signed=True) for _ in range(40)]
+        xs = [x for x in xs if -lim <= x < lim]
+        L = np.array([modular.to_limbs(x, W) for x in xs], dtype=np.uint32)
+        assert certificate.limbs_mod_q(L, q).tolist() == [x % q for x in xs]
+
+
+@pytest.mark.parametrize("degs", [(3,), (2, 4), (1, 0, 2), (2, 1, 1, 3)])
+def test_horner_u64_equals_the_monomial_sum(degs):
+    rng = np.random.default_rng(sum(degs) + 11)
+    q = certificate.Q31
+    size = int(np.prod([d + 1 for d in degs]))
+    vec = [int(x) for x in rng.integers(0, q, size)]
+    point = [int(x) for x in rng.integers(1, q - 1, len(degs))]
+    box = np.array(vec, dtype=np.int64).reshape([d + 1 for d in degs])
+    assert int(certificate._horner_u64(box, point, q)) == certificate._eval_dense(vec, degs, point, q)
+
+
+def test_check_limbs_accepts_truth_and_rejects_planted_errors():
+    rng = np.random.default_rng(43)
+    pm = rand_matrix(rng, 4, (2, 1, 1), 0.7, -1000, 1000)
+    det = bareiss.det_packed(pm.coeffs.tolist(), pm.degs)
+    D = plan.det_degree_bound(4, pm.degs)
+    W = 3
+    L = np.array([modular.to_limbs(x, W) for x in det], dtype=np.uint32)
+    assert certificate.check_limbs(pm.coeffs, pm.degs, L, D)
+    for j in rng.choice(len(det), 12, replace=False):
+        bad = L.copy()
+        bad[j, int(rng.integers(0, W))] ^= np.uint32(1 << int(rng.integers(0, 32)))
+        assert not certificate.check_limbs(pm.coeffs, pm.degs, bad, D, trials=2)
