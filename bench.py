@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
+    ap.add_argument("--no-structured", action="store_true")
     ap.add_argument("--served-jobs", type=int, default=300)
     return ap.parse_args()
 
@@ -320,11 +321,18 @@ def _timed_steps(runner, st, flush, steps, stage_timer):
 
 def served_leg(args, mats, batched_value, st):
     """The served workload: a seeded Poisson stream of the batched
-    distribution plus 5 % 32x32 jobs over Z[x, y] (degree 6), at 60 % of the
-    batched throughput; continuous batching with admission by predicted
-    memory.  Once with the MLP trained on the method's own timings, once with
-    the analytic bound alone (same stream)."""
+    distribution plus 5 % 32x32 jobs over Z[x, y] (degree 6), continuous
+    batching with admission by predicted memory.  First the server's
+    capacity (the same jobs all waiting at t = 0, MLP admission, an ample
+    budget), then a sweep of arrival rates at 0.5x, 1x and 2x that capacity
+    under a memory budget that binds (a quarter of the MLP's predicted peak
+    at capacity), once per admission policy: the MLP trained on the method's
+    own timings, the analytic bound calibrated by its median ratio to the
+    measurements, and the raw bound.  Each run reports p50/p99 latency,
+    dets/s and the device memory its waves actually held at peak against the
+    budget."""
     import numpy as np
+    import torch
     from paper_2010_12117_gb300 import synth
     from paper_2010_12117_gb300.predictor import Predictor
     from paper_2010_12117_gb300.serve import Server, calibrate
@@ -335,24 +343,39 @@ def served_leg(args, mats, batched_value, st):
     pr = Predictor(seed=args.seed)
     pr.fit(X, Y, Bd, steps=2000)
     train_s = time.perf_counter() - t0
-    rate = 0.6 * batched_value
-    stream = synth.served_stream(args.seed, args.served_jobs, rate=rate)
-    out = {"rate_jobs_per_s": rate, "jobs": args.served_jobs, "calibration_jobs": len(cal),
-           "calibrate_and_train_s": train_s, "budget_bytes": 40e9, "slots": 3}
-    for name, p in (("mlp", pr), ("analytic", Predictor(seed=args.seed))):
-        srv = Server(p, mem_budget=40e9, slots=3, wave_seconds=0.02)
-        rep = srv.run(stream, keep_results=False)
-        out[name] = rep.summary()
-    # capacity: the same jobs all waiting at t = 0 (MLP admission), against the
-    # plain per-matrix form over the same jobs (one pass, CUDA events)
-    import torch
+    calibrated = Predictor(seed=args.seed)
+    calibrated.ratio = pr.ratio.copy()  # untrained: the bound times the measured median ratio
+    policies = (("mlp", pr), ("calibrated_bound", calibrated), ("raw_bound", Predictor(seed=args.seed)))
+    base_stream = synth.served_stream(args.seed, args.served_jobs, rate=1.0)
+    backlog = [synth.Arrival(0.0, a.job) for a in base_stream]
+
+    def run(pred, arrivals, budget):
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        rep = Server(pred, mem_budget=budget, slots=3, wave_seconds=0.02).run(arrivals, keep_results=False)
+        torch.cuda.synchronize()
+        actual = float(torch.cuda.max_memory_allocated() - base)
+        return dict(rep.summary(), budget_bytes=budget, actual_peak_bytes=actual,
+                    over_budget=actual > budget)
+
+    run(pr, backlog[:40], 200e9)  # warm: plan tables, batch resources, allocator
+    cap = run(pr, backlog, 200e9)
+    capacity = cap["exact_dets_per_s"]
+    budget = 0.25 * cap["peak_predicted_mem_bytes"]
+    out = {"jobs": args.served_jobs, "calibration_jobs": len(cal), "calibrate_and_train_s": train_s,
+           "slots": 3, "capacity": cap, "binding_budget_bytes": budget, "rates": {}}
+    for frac in (0.5, 1.0, 2.0):
+        rate = frac * capacity
+        stream = synth.served_stream(args.seed, args.served_jobs, rate=rate)
+        out["rates"][f"{frac}x"] = {"rate_jobs_per_s": rate}
+        for name, p in policies:
+            out["rates"][f"{frac}x"][name] = run(p, stream, budget)
+    # the plain per-matrix form over the same jobs (one pass, CUDA events)
     from paper_2010_12117_gb300.runner import PlainRunner
-    backlog = [synth.Arrival(0.0, a.job) for a in stream]
-    rep = Server(pr, mem_budget=40e9, slots=3, wave_seconds=0.02).run(backlog, keep_results=False)
-    out["saturated"] = rep.summary()
     torch.cuda.synchronize()
     w0 = time.perf_counter()
-    plain = PlainRunner([a.job for a in stream])  # plans, buffers, upload, run, download
+    plain = PlainRunner([a.job for a in base_stream])  # plans, buffers, upload, run, download
     plain.upload(st)
     plain.compute(st)
     plain.download(st)
@@ -366,8 +389,8 @@ def served_leg(args, mats, batched_value, st):
     e_ev.synchronize()
     ms = s_ev.elapsed_time(e_ev)
     plain.close()
-    out["plain_same_jobs"] = {"wall_s": wall, "exact_dets_per_s": len(stream) / wall,
-                              "device_ms": ms, "device_exact_dets_per_s": len(stream) / (ms * 1e-3),
+    out["plain_same_jobs"] = {"wall_s": wall, "exact_dets_per_s": len(base_stream) / wall,
+                              "device_ms": ms, "device_exact_dets_per_s": len(base_stream) / (ms * 1e-3),
                               "note": "wall: plans, buffers, upload, one pass, download (like the "
                                       "server's waves); device: one pass with inputs resident"}
     return out
@@ -490,6 +513,122 @@ def eval_totals(mats, st, hbm_peak):
         pl.close()
     return {"ms": ms_total, "GBps": byts / ms_total / 1e6, "frac": byts / ms_total / 1e6 / hbm_peak,
             "algorithmic_bytes": byts, "bound": "hbm", "launch_groups": len(evs)}
+
+
+def structured_leg(st, hbm_peak, derived_upd):
+    """Sec. 3.1's large-degree case and Sec. 5/6's repeated entries.
+
+    (1) The 15 x 15 Sylvester matrix over Z[x1..x4] with determinant degrees
+    (298, 171, 119, 45): 2.8e8 nodes per prime, evaluation + condensation
+    streamed slab by slab through a fixed workspace (the lowest-degree
+    variable first: its nodes are the slabs), then interpolation and CRT;
+    once with the entry map (17 distinct entries + the zero one of 225) in a
+    24 GB workspace, once with all 225 entries in 64 GB (one prime's
+    evaluated matrices would take 255 GB).  (2) The 16 x 16 Sylvester
+    workload's evaluation with and without the entry map (18 distinct of
+    256 entries)."""
+    import numpy as np
+    import torch
+    from paper_2010_12117_gb300 import synth
+    from paper_2010_12117_gb300.binding import Plan, det_degree_bound, entry_degrees, unique_entries
+    from paper_2010_12117_gb300.pipeline import permute_coeffs, prime_count
+    from paper_2010_12117_gb300.runner import condense_updates
+
+    def ev_pair():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    out = {}
+    pm = synth.sylvester_15_four_vars(0)
+    order = sorted(range(pm.nvars), key=lambda v: (pm.degs[v], v))
+    cp = permute_coeffs(pm.coeffs, pm.degs, order)
+    dp = tuple(pm.degs[v] for v in order)
+    D = det_degree_bound(entry_degrees(cp, dp), len(dp))
+    P = prime_count(pm.coeffs)
+    m, U, uniq = unique_entries(cp)
+    for name, use_map, budget in (("entry_map_24GB", True, 24 << 30), ("all_entries_64GB", False, 64 << 30)):
+        pl = Plan(pm.n, dp, P, det_degs=D)
+        rows = np.ascontiguousarray(cp, dtype=np.int32).reshape(pm.n * pm.n, -1)
+        if use_map:
+            pl.set_entry_map(m, U)
+            rows = uniq
+        c = torch.from_numpy(np.ascontiguousarray(rows, dtype=np.int32).reshape(-1)).cuda()
+        ws_words = max(pl.stream_ws_words(1), pl.interp_ws_words, min(pl.stream_ws_words(pl.M[0]), budget // 4))
+        ws = torch.empty(ws_words, dtype=torch.int32, device="cuda")
+        detv = torch.empty(pl.G, dtype=torch.int32, device="cuda")
+        res = torch.empty(P * pl.C, dtype=torch.int32, device="cuda")
+        limbs = torch.empty(pl.C * pl.W, dtype=torch.int32, device="cuda")
+        pl.eval_condense(c, 0, 1, detv, ws, st)  # warm: module load, attributes
+        st.synchronize()
+        marks = {"eval_condense": [], "interp": [], "crt": []}
+        for q in range(P):
+            a, b = ev_pair()
+            a.record(st)
+            pl.eval_condense(c, q, q + 1, detv, ws, st)
+            b.record(st)
+            marks["eval_condense"].append((a, b))
+            a, b = ev_pair()
+            a.record(st)
+            pl.interp(detv, q, q + 1, res[q * pl.C:(q + 1) * pl.C], ws, st)
+            b.record(st)
+            marks["interp"].append((a, b))
+        a, b = ev_pair()
+        a.record(st)
+        pl.crt(res, limbs, st)
+        b.record(st)
+        marks["crt"].append((a, b))
+        st.synchronize()
+        status = pl.sync_status(st)
+        ms = {k: sum(x.elapsed_time(y) for x, y in v) for k, v in marks.items()}
+        upd = float(P) * pl.G * condense_updates(pm.n)
+        row_words = pl.entries * -(-(pl.G // pl.M[0]) // 32) * 32
+        slab_rows = min(pl.M[0], max(1, (ws_words - pl.items * (pl.G // pl.M[0]) * (pl.d[0] + 1)) // row_words))
+        out[name] = {"n": pm.n, "det_degrees_in_order": [int(x) for x in pl.D], "variable_order": order,
+                     "P": P, "G": pl.G, "C": pl.C, "W": pl.W, "entries_per_prime": pl.entries,
+                     "evaluated_bytes_per_prime": 4.0 * pl.entries * pl.G,
+                     "workspace_bytes": 4.0 * ws_words, "approx_slab_rows_of_x1": int(slab_rows),
+                     "ms": ms, "total_ms": sum(ms.values()), "status": status,
+                     "modp_dets_per_s": P * pl.G / (ms["eval_condense"] * 1e-3),
+                     "eval_condense_Gupdate_s": upd / (ms["eval_condense"] * 1e-3) / 1e9,
+                     "eval_condense_alu_frac": upd / (ms["eval_condense"] * 1e-3) / derived_upd,
+                     "bound": "alu"}
+        pl.close()
+        del c, ws, detv, res, limbs
+        torch.cuda.empty_cache()
+    # the 16 x 16 Sylvester workload: evaluation with and without the map
+    pm = synth.sylvester_16(0)
+    P = prime_count(pm.coeffs)
+    m, U, uniq = unique_entries(pm.coeffs)
+    res16 = {}
+    for name, use_map in (("all_entries", False), ("entry_map", True)):
+        pl = Plan(pm.n, pm.degs, P)
+        rows = np.ascontiguousarray(pm.coeffs, dtype=np.int32).reshape(pm.n * pm.n, -1)
+        if use_map:
+            pl.set_entry_map(m, U)
+            rows = uniq
+        c = torch.from_numpy(np.ascontiguousarray(rows, dtype=np.int32).reshape(-1)).cuda()
+        ev = torch.empty(P * pl.entries * pl.G, dtype=torch.int32, device="cuda")
+        dv = torch.empty(P * pl.G, dtype=torch.int32, device="cuda")
+        wsb = pl.workspace(P)
+        pl.eval(c, 0, P, ev, wsb, st)
+        reps = 200
+        a, b = ev_pair()
+        a.record(st)
+        for _ in range(reps):
+            pl.eval(c, 0, P, ev, wsb, st)
+        b.record(st)
+        a2, b2 = ev_pair()
+        a2.record(st)
+        for _ in range(reps):
+            pl.condense(ev, 0, P, dv, st)
+        b2.record(st)
+        st.synchronize()
+        res16[name] = {"entries_per_prime": pl.entries, "evals_bytes": 4.0 * P * pl.entries * pl.G,
+                       "eval_us": 1e3 * a.elapsed_time(b) / reps, "condense_us": 1e3 * a2.elapsed_time(b2) / reps}
+        pl.close()
+    res16["eval_bytes_ratio"] = res16["all_entries"]["evals_bytes"] / res16["entry_map"]["evals_bytes"]
+    res16["eval_time_ratio"] = res16["all_entries"]["eval_us"] / res16["entry_map"]["eval_us"]
+    out["sylvester_16x16_eval"] = res16
+    return out
 
 
 def run_ours(args, world, rank, local):
@@ -661,6 +800,7 @@ def run_ours(args, world, rank, local):
 
     served = None if args.no_served else served_leg(args, mats, value, st)
     kernels = None if args.no_kernels else kernel_leg(st, hbm_peak, mats)
+    structured = None if args.no_structured else structured_leg(st, hbm_peak, derived_upd)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -710,6 +850,7 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "served": served,
         "hbm_kernels": kernels,
+        "structured": structured,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -125,11 +125,17 @@ int polydet_hadamard_primes(int n, const int64_t *entry_l1, int *nprimes_out,
 
 /* Build a plan for n x n matrices in `nvars` variables whose entries have
  * degree <= entry_deg[v] (host array) in x_v, using the first `nprimes`
- * primes of the table (must be >= 1).  Allocates the plan's small device
- * tables (Montgomery constants, twiddles, Garner tables, status word); no
- * later call allocates device memory: scratch is passed in by the caller.
- * `flags` is 0 or POLYDET_FLAG_FULL_GRID.  The plan must be destroyed with
- * polydet_plan_destroy. */
+ * primes of the table (must be >= 1).  The plan's small device tables
+ * (Montgomery constants, twiddles, Garner and interpolation tables) are
+ * shared by every plan of the same shape (n, degrees, prime count, grid, on
+ * one device): the first plan of a shape allocates and uploads them as one
+ * block, later plans of that shape copy nothing and allocate only their
+ * status word, and the block is kept after the last such plan is destroyed
+ * (up to 256 unused shapes, least recently used dropped first;
+ * polydet_plan_cache_clear frees them).  No later call allocates device
+ * memory: scratch is passed in by the caller.  `flags` is 0 or
+ * POLYDET_FLAG_FULL_GRID.  The plan must be destroyed with
+ * polydet_plan_destroy, after the work enqueued with it has completed. */
 int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
                  int nprimes, uint32_t flags);
 
@@ -173,6 +179,8 @@ int polydet_unique_entries(int n, int64_t E, const int32_t *coeffs, int32_t *map
  * evals tensor shrink by n^2 / (U + 1). */
 int polydet_plan_set_entry_map(polydet_plan_t plan, const int32_t *map, int U);
 int polydet_plan_destroy(polydet_plan_t plan);
+/* Free the shared tables of every shape that no live plan uses. */
+int polydet_plan_cache_clear(void);
 int polydet_plan_query(polydet_plan_t plan, polydet_plan_info *info);
 /* Host copies: primes [P]; roots w_{q,v} as [P][nvars]. */
 int polydet_plan_primes(polydet_plan_t plan, uint32_t *primes_out);
@@ -342,8 +350,13 @@ typedef struct polydet_batch_info {
 #define POLYDET_OFF_RESIDUES 3
 #define POLYDET_OFF_LIMBS 4
 
-/* Plan a batch from host `jobs[njobs]` (one polydet_plan per job is built;
- * small device tables only).  flags must be 0. */
+/* Plan a batch from host `jobs[njobs]` (one polydet_plan per job, with the
+ * shared tables of polydet_plan).  The batch's streams, events, status word
+ * and segment tables come from a per-process pool and return to it when the
+ * batch is destroyed, so planning batch after batch creates no stream and
+ * allocates nothing once the pool and the shape cache are warm.  Destroy a
+ * batch only after the work enqueued with it has completed.  flags must be
+ * 0. */
 int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs, int njobs, uint32_t flags);
 int polydet_batch_destroy(polydet_batch_t batch);
 int polydet_batch_query(polydet_batch_t batch, polydet_batch_info *info);

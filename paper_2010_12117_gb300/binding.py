@@ -86,6 +86,7 @@ SIGNATURES = {
     "polydet_stream_ws_words": (ctypes.c_uint64, [_VP, _I]),
     "polydet_eval_condense": (_I, [_VP, _VP, _I, _I, _VP, _VP, ctypes.c_uint64, _VP]),
     "polydet_plan_destroy": (_I, [_VP]),
+    "polydet_plan_cache_clear": (_I, []),
     "polydet_plan_query": (_I, [_VP, ctypes.POINTER(PlanInfo)]),
     "polydet_plan_primes": (_I, [_VP, _PU32]),
     "polydet_plan_roots": (_I, [_VP, _PU32]),

@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -30,6 +31,87 @@ int pow2_at_least(int x) {
   return v;
 }
 }  // namespace
+
+// The streams, events, status word and segment-table buffer a batch needs,
+// recycled through a per-process pool: a batch takes a set when it is planned
+// and returns it when destroyed, so batches planned one after another (a
+// server's waves) create no stream or event and allocate nothing but a
+// larger segment buffer when one is needed.
+struct BatchRes {
+  int dev = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev[6] = {};
+  cudaStream_t fan[kFan] = {};
+  cudaEvent_t fev[kFan + 1] = {};
+  uint32_t *d_status = nullptr;
+  FusedSeg *segs = nullptr;
+  size_t segs_cap = 0;
+};
+
+static std::mutex g_res_mu;
+static std::vector<BatchRes *> g_res_free;
+
+static void free_res(BatchRes *r) {
+  if (!r) return;
+  for (auto e : r->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto e : r->fev)
+    if (e) cudaEventDestroy(e);
+  if (r->side) cudaStreamDestroy(r->side);
+  for (auto f : r->fan)
+    if (f) cudaStreamDestroy(f);
+  cudaFree(r->d_status);
+  cudaFree(r->segs);
+  delete r;
+}
+
+static int take_res(BatchRes **out) {
+  int dev = 0;
+  PD_CUDA(cudaGetDevice(&dev));
+  BatchRes *r = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_res_mu);
+    for (size_t i = 0; i < g_res_free.size(); ++i) {
+      if (g_res_free[i]->dev == dev) {
+        r = g_res_free[i];
+        g_res_free.erase(g_res_free.begin() + i);
+        break;
+      }
+    }
+  }
+  if (!r) {
+    r = new BatchRes();
+    r->dev = dev;
+    // the materialized orders' first-variable passes run on the side stream
+    // at the highest priority: their CTAs take SM slots as soon as
+    // condensation CTAs retire, so the HBM-bound passes run beside the
+    // integer-bound condensation instead of after it
+    int least = 0, greatest = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&r->side, cudaStreamNonBlocking, greatest) == cudaSuccess &&
+              cudaMalloc((void **)&r->d_status, sizeof(uint32_t)) == cudaSuccess;
+    for (auto &e : r->ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    for (auto &e : r->fev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    for (auto &f : r->fan) ok = ok && cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+      free_res(r);
+      return POLYDET_ECUDA;
+    }
+  }
+  // a fresh status word (the set's previous batch has been destroyed)
+  if (cudaMemset(r->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+    free_res(r);
+    return POLYDET_ECUDA;
+  }
+  *out = r;
+  return POLYDET_OK;
+}
+
+static void give_res(BatchRes *r) {
+  if (!r) return;
+  std::lock_guard<std::mutex> lock(g_res_mu);
+  g_res_free.push_back(r);
+}
 
 struct polydet_batch_s {
   int njobs = 0;
@@ -53,15 +135,16 @@ struct polydet_batch_s {
   // caller's stream; ev[0..1] = pass of buffer b done, ev[2..3] = condensation
   // of buffer b done, ev[4] / ev[5] = fork / join
   cudaStream_t side = nullptr;
-  cudaEvent_t ev[6] = {};
+  cudaEvent_t *ev = nullptr;
   // per-job launches of stages 1, 3, 4 fan out over kFan streams (job j on
   // fan[j % kFan], with its own scratch slice), joined back by events
-  cudaStream_t fan[kFan] = {};
-  cudaEvent_t fev[kFan + 1] = {};
+  cudaStream_t *fan = nullptr;
+  cudaEvent_t *fev = nullptr;
   uint64_t scratch_stride = 0;
   // one status word for every job of the batch (each job plan points at
   // it), so that reading the batch's status is one copy, not one per job
   uint32_t *d_status = nullptr;
+  BatchRes *res = nullptr;  // the pooled set the pointers above come from
 };
 
 static int fan_begin(polydet_batch_s *b, cudaStream_t st) {
@@ -112,15 +195,7 @@ static void update_ws(polydet_batch_s *b) {
 static void destroy_batch(polydet_batch_s *b) {
   if (!b) return;
   for (auto p : b->plans) polydet_plan_destroy(p);
-  cudaFree(b->d_status);
-  for (int n = 0; n <= POLYDET_MAX_N; ++n) cudaFree(b->d_segs[n]);
-  for (auto e : b->ev)
-    if (e) cudaEventDestroy(e);
-  for (auto e : b->fev)
-    if (e) cudaEventDestroy(e);
-  if (b->side) cudaStreamDestroy(b->side);
-  for (auto f : b->fan)
-    if (f) cudaStreamDestroy(f);
+  give_res(b->res);
   delete b;
 }
 
@@ -154,7 +229,6 @@ static int build_class(polydet_batch_s *b, int n) {
   if (bps < 1) return POLYDET_EINVAL;  // the CTA's shared memory does not fit
   b->nbuf[n] = nbuf;
   b->blocks[n] = (int)std::min<int64_t>(it, (int64_t)bps * b->sms);
-  if (!b->d_segs[n]) PD_CUDA(cudaMalloc((void **)&b->d_segs[n], v.size() * sizeof(FusedSeg)));
   PD_CUDA(cudaMemcpy(b->d_segs[n], v.data(), v.size() * sizeof(FusedSeg), cudaMemcpyHostToDevice));
   return POLYDET_OK;
 }
@@ -170,11 +244,18 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
     delete b;
     return POLYDET_ECUDA;
   }
-  if (cudaMalloc((void **)&b->d_status, sizeof(uint32_t)) != cudaSuccess ||
-      cudaMemset(b->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
-    destroy_batch(b);
-    return POLYDET_ENOMEM;
+  {
+    const int rc = take_res(&b->res);
+    if (rc) {
+      delete b;
+      return rc;
+    }
   }
+  b->side = b->res->side;
+  b->ev = b->res->ev;
+  b->fan = b->res->fan;
+  b->fev = b->res->fev;
+  b->d_status = b->res->d_status;
   b->coeff_off.assign(1, 0);
   b->part_off.assign(1, 0);
   b->det_off.assign(1, 0);
@@ -186,15 +267,12 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
       destroy_batch(b);
       return POLYDET_EINVAL;
     }
-    polydet_plan_t pl = nullptr;
-    int rc = polydet_plan(&pl, jb.n, jb.nvars, jb.d, jb.nprimes, jb.flags);
+    polydet_plan_t pl = nullptr;  // reports into the batch's status word
+    int rc = pd_plan_impl(&pl, jb.n, jb.nvars, jb.d, nullptr, jb.nprimes, jb.flags, b->d_status);
     if (rc) {
       destroy_batch(b);
       return rc;
     }
-    cudaFree(pl->d_status);  // the job reports into the batch's word
-    pl->d_status = b->d_status;
-    pl->status_shared = 1;
     b->plans.push_back(pl);
     const int k = pl->nvars;
     const int L = pl->d[k - 1] + 1;
@@ -216,28 +294,6 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
   for (int n = 1; n <= POLYDET_MAX_N; ++n)
     b->mode[n] = n >= POLYDET_BATCH_MATERIALIZE_N ? POLYDET_BATCH_MATERIALIZED : POLYDET_BATCH_FUSED;
   update_ws(b);
-  if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) {
-    destroy_batch(b);
-    return POLYDET_ECUDA;
-  }
-  for (auto &e : b->ev) {
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-      destroy_batch(b);
-      return POLYDET_ECUDA;
-    }
-  }
-  for (auto &e : b->fev) {
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-      destroy_batch(b);
-      return POLYDET_ECUDA;
-    }
-  }
-  for (auto &f : b->fan) {
-    if (cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking) != cudaSuccess) {
-      destroy_batch(b);
-      return POLYDET_ECUDA;
-    }
-  }
   for (int j = 0; j < njobs; ++j) {
     polydet_plan_s *pl = b->plans[j];
     const int k = pl->nvars;
@@ -259,6 +315,23 @@ extern "C" int polydet_batch_plan(polydet_batch_t *out, const polydet_job *jobs,
       s.status = pl->d_status;
       b->segs[pl->n].push_back(s);
     }
+  }
+  // the segment tables of every order in the pooled buffer (grown if needed)
+  size_t nseg = 0;
+  for (int n = 1; n <= POLYDET_MAX_N; ++n) nseg += b->segs[n].size();
+  if (nseg > b->res->segs_cap) {
+    cudaFree(b->res->segs);
+    b->res->segs = nullptr;
+    b->res->segs_cap = 0;
+    if (cudaMalloc((void **)&b->res->segs, nseg * sizeof(FusedSeg)) != cudaSuccess) {
+      destroy_batch(b);
+      return POLYDET_ENOMEM;
+    }
+    b->res->segs_cap = nseg;
+  }
+  for (int n = 1, at = 0; n <= POLYDET_MAX_N; ++n) {
+    b->d_segs[n] = b->res->segs + at;
+    at += (int)b->segs[n].size();
   }
   for (int n = 1; n <= POLYDET_MAX_N; ++n) {
     b->threads[n] = 128;

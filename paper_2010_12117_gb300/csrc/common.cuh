@@ -69,6 +69,7 @@ struct polydet_plan_s {
   uint32_t *d_mfull;      // [W] M
   uint32_t *d_status;     // 1 word
   int status_shared;      // 1: d_status belongs to a batch (one word for all its jobs)
+  void *tables;           // the shape's shared device tables (plan.cu's cache entry)
   // entries: evaluated matrix entry e = i n + j of a node is entry ent[e] of
   // the evals tensor, which holds nent entries per prime; nitems of them are
   // evaluated from coefficients (all n^2 by default; with an entry map the U
@@ -90,6 +91,11 @@ void pd_set_error(const char *what, cudaError_t e);
       return POLYDET_ECUDA;                  \
     }                                        \
   } while (0)
+
+// Plan construction (plan.cu); `shared_status`, when not null, is the status
+// word the plan reports into (a batch's), else the plan allocates its own.
+int pd_plan_impl(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
+                 const int32_t *det_deg, int nprimes, uint32_t flags, uint32_t *shared_status);
 
 // Per-device one-time set-up of a call site (kernel attributes such as the
 // dynamic shared-memory limit are per device): runs `set` the first time the

@@ -54,6 +54,9 @@ struct TxArgs {
   // register-direct kernel takes a window only in coset order, with row_lo
   // a multiple of the coset size
   int row_lo, row_hi;
+  // items from zero_item_plus1 - 1 on read nothing and write zeros (the zero
+  // entry of an entry map, one item past the evaluated ones); 0: none
+  int zero_item_plus1;
 };
 
 // Output rows one column of a pass stores.
@@ -83,7 +86,8 @@ __global__ void __launch_bounds__(256) coltx_kernel(TxArgs a) {
     }
     const int64_t col = col0 + c;
     uint32_t v = 0;
-    if (r < a.Lin && col < ncols) {
+    const bool zero_item = a.zero_item_plus1 && (int)blockIdx.y >= a.zero_item_plus1 - 1;
+    if (r < a.Lin && col < ncols && !zero_item) {
       const int64_t aa = col / a.B, bb = col - aa * a.B;
       const int64_t idx = in_base + (aa * a.Lin + r) * a.B + bb;
       v = a.in_is_i32 ? reduce_i32(((const int32_t *)a.in)[idx], md.p) : ((const uint32_t *)a.in)[idx];
@@ -235,10 +239,13 @@ __global__ void __launch_bounds__(256) coltx_direct_kernel(TxArgs a) {
     const bool ok = col < ncols;
     const int64_t cc = ok ? col : col0;
     const int64_t aa = (a.A == 1) ? 0 : cc / a.B, bb = cc - aa * a.B;
+    const bool zero_item = a.zero_item_plus1 && item >= a.zero_item_plus1 - 1;
 #pragma unroll
     for (int e = 0; e < LIN; ++e) {
       const int64_t idx = in_base + (aa * LIN + e) * a.B + bb;
-      c[k][e] = a.in_is_i32 ? reduce_i32(((const int32_t *)a.in)[idx], p) : ((const uint32_t *)a.in)[idx];
+      c[k][e] = zero_item ? 0u
+                          : (a.in_is_i32 ? reduce_i32(((const int32_t *)a.in)[idx], p)
+                                         : ((const uint32_t *)a.in)[idx]);
     }
     int64_t obase;
     if (a.il_L)
@@ -431,10 +438,6 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
   // with an entry map only the distinct entries are evaluated, and the zero
   // entry's slot is cleared
   const int64_t items = pl->nitems, nent = pl->nent;
-  if (nent > items)
-    PD_CUDA(cudaMemset2DAsync(evals + items * pl->G, (size_t)nent * pl->G * sizeof(uint32_t), 0,
-                              (size_t)(nent - items) * pl->G * sizeof(uint32_t), (size_t)np, st));
-  if (items == 0) return POLYDET_OK;
   const void *cur_in = coeffs;
   int64_t cur_item = pl->E, cur_prime = 0;
   int cur_i32 = 1;
@@ -472,8 +475,17 @@ extern "C" int polydet_eval(polydet_plan_t pl, const int32_t *coeffs, int lo, in
     a.nvars = k;
     a.var = v;
     a.status = pl->d_status;
-    int rc = launch_pass(a, (int)items, np, st);
-    if (rc) return rc;
+    // the last pass also writes the zero entry's slot (entry map): one more
+    // item that reads nothing; earlier passes skip a map without entries
+    int launch_items = (int)items;
+    if (v == 0 && nent > items) {
+      a.zero_item_plus1 = (int)items + 1;
+      launch_items = (int)nent;
+    }
+    if (launch_items > 0) {
+      int rc = launch_pass(a, launch_items, np, st);
+      if (rc) return rc;
+    }
     cur_in = a.out;
     cur_item = a.out_item_stride;
     cur_prime = a.out_prime_stride;
@@ -871,10 +883,7 @@ int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int head_q0, in
     a.row_lo = row_lo;
     a.row_hi = row_hi;
   }
-  if (nent > items)  // the zero entry's slot (entry map)
-    PD_CUDA(cudaMemset2DAsync(evals + items * lay.entry, (size_t)nent * lay.entry * sizeof(uint32_t), 0,
-                              (size_t)(nent - items) * lay.entry * sizeof(uint32_t), (size_t)(hi - lo), st));
-  if (items == 0) return POLYDET_OK;
+  if (nent > items) a.zero_item_plus1 = (int)items + 1;  // the zero entry's slot (entry map)
   a.in = head + (int64_t)(lo - head_q0) * items * S1;
   a.in_item_stride = S1;
   a.in_prime_stride = items * S1;
@@ -883,7 +892,7 @@ int pd_eval_tail(const polydet_plan_s *pl, const uint32_t *head, int head_q0, in
   a.out_row = lay.rowstride;
   a.out_item_stride = lay.entry;
   a.out_prime_stride = nent * lay.entry;
-  return launch_pass(a, (int)items, hi - lo, st);
+  return launch_pass(a, (int)nent, hi - lo, st);
 }
 
 uint64_t pd_partial_ws_words(const polydet_plan_s *pl) {

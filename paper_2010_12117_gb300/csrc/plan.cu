@@ -327,48 +327,146 @@ static void interp_tables(uint32_t p32, uint32_t w32, int N, int L, int M, uint3
   cache.emplace(key, std::vector<uint32_t>(dst, dst + words));
 }
 
+// ---------------------------------------------------------------------------
+// Plan tables are shared by every plan of the same shape (order, variables,
+// entry and determinant degrees, primes, grid): one packed device block per
+// shape, built on the first plan of that shape and kept, once its last plan
+// is gone, until more than kCacheShapes unused shapes are held (least
+// recently used first) or polydet_plan_cache_clear() is called.  A plan of
+// a cached shape is a host copy of the shape's template plan: no host table
+// is recomputed and no device memory is allocated for it (its status word
+// aside, which a batch provides for its jobs).
+// ---------------------------------------------------------------------------
+namespace {
+struct PlanTables {
+  void *dev = nullptr;  // every device table of the shape, packed
+  int refs = 0;
+  uint64_t last_use = 0;
+  bool cached = false;             // held by g_cache (else freed with its last plan)
+  polydet_plan_s *tmpl = nullptr;  // host template: the plan's fields with device pointers set
+};
+constexpr size_t kCacheShapes = 256;
+std::mutex g_cache_mu;
+std::map<std::vector<int64_t>, PlanTables *> g_cache;
+uint64_t g_cache_clock = 0;
+
+std::vector<int64_t> shape_key(int dev, int n, int nvars, const int *d, const int *D, int P, int full) {
+  std::vector<int64_t> k = {dev, n, nvars, P, full};
+  for (int v = 0; v < nvars; ++v) {
+    k.push_back(d[v]);
+    k.push_back(D[v]);
+  }
+  return k;
+}
+
+void drop_unused(size_t keep) {  // with g_cache_mu held
+  while (true) {
+    size_t unused = 0;
+    auto victim = g_cache.end();
+    for (auto it = g_cache.begin(); it != g_cache.end(); ++it) {
+      if (it->second->refs) continue;
+      ++unused;
+      if (victim == g_cache.end() || it->second->last_use < victim->second->last_use) victim = it;
+    }
+    if (unused <= keep || victim == g_cache.end()) return;
+    cudaFree(victim->second->dev);
+    delete victim->second->tmpl;
+    delete victim->second;
+    g_cache.erase(victim);
+  }
+}
+}  // namespace
+
 static void free_plan(polydet_plan_s *pl) {
   if (!pl) return;
-  cudaFree(pl->d_mod);
-  cudaFree(pl->d_tw_fwd);
-  cudaFree(pl->d_tw_inv);
-  cudaFree(pl->d_ninv);
-  cudaFree(pl->d_rn);
-  cudaFree(pl->d_garner);
-  cudaFree(pl->d_mhalf);
-  cudaFree(pl->d_mfull);
   if (!pl->status_shared) cudaFree(pl->d_status);
-  cudaFree(pl->d_itab);
+  if (pl->tables) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    PlanTables *t = static_cast<PlanTables *>(pl->tables);
+    if (--t->refs == 0 && !t->cached) {
+      cudaFree(t->dev);
+      delete t->tmpl;
+      delete t;
+    }
+    drop_unused(kCacheShapes);
+  }
   delete pl;
 }
 
-template <class T>
-static int upload(T **dst, const std::vector<T> &src) {
-  size_t bytes = src.size() * sizeof(T);
-  if (bytes == 0) bytes = sizeof(T);
-  cudaError_t e = cudaMalloc((void **)dst, bytes);
-  if (e != cudaSuccess) {
-    pd_set_error("cudaMalloc", e);
-    return POLYDET_ENOMEM;
-  }
-  if (!src.empty()) {
-    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      pd_set_error("cudaMemcpy", e);
-      return POLYDET_ECUDA;
-    }
-  }
+extern "C" int polydet_plan_cache_clear(void) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  drop_unused(0);
   return POLYDET_OK;
 }
 
-static int plan_impl(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
-                     const int32_t *det_deg, int nprimes, uint32_t flags) {
+// Bytes of a packed table block and the offset of each table (256-byte aligned).
+struct Packer {
+  std::vector<uint8_t> host;
+  template <class T>
+  size_t add(const std::vector<T> &v) {
+    const size_t off = (host.size() + 255) / 256 * 256;
+    host.resize(off + std::max<size_t>(v.size() * sizeof(T), sizeof(T)), 0);
+    if (!v.empty()) memcpy(host.data() + off, v.data(), v.size() * sizeof(T));
+    return off;
+  }
+};
+
+// The plan's own status word (or the batch's), then hand it out.
+static int finish_plan(polydet_plan_s *pl, uint32_t *shared_status, polydet_plan_t *out) {
+  if (shared_status) {
+    pl->d_status = shared_status;
+    pl->status_shared = 1;
+  } else {
+    pl->status_shared = 0;
+    pl->d_status = nullptr;
+    cudaError_t e = cudaMalloc((void **)&pl->d_status, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(pl->d_status, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+      pd_set_error("cudaMalloc (status word)", e);
+      pl->status_shared = 1;  // nothing of its own to free
+      free_plan(pl);
+      return POLYDET_ENOMEM;
+    }
+  }
+  *out = pl;
+  return POLYDET_OK;
+}
+
+int pd_plan_impl(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
+                 const int32_t *det_deg, int nprimes, uint32_t flags, uint32_t *shared_status) {
   if (!out || n < 1 || n > POLYDET_MAX_N || nvars < 1 || nvars > POLYDET_MAX_VARS ||
       !entry_deg || (flags & ~POLYDET_FLAG_FULL_GRID))
     return POLYDET_EINVAL;
   const auto &table = prime_table();
   if (nprimes < 1) return POLYDET_EINVAL;
   if (nprimes > (int)table.size()) return POLYDET_EPRIMES;
+  int dev_id = 0;
+  PD_CUDA(cudaGetDevice(&dev_id));
+  std::vector<int64_t> key;
+  {
+    int dd[POLYDET_MAX_VARS], DD[POLYDET_MAX_VARS];
+    for (int v = 0; v < nvars; ++v) {
+      if (entry_deg[v] < 0) return POLYDET_EINVAL;
+      dd[v] = entry_deg[v];
+      DD[v] = det_deg ? det_deg[v] : n * entry_deg[v];
+    }
+    key = shape_key(dev_id, n, nvars, dd, DD, nprimes, (flags & POLYDET_FLAG_FULL_GRID) ? 1 : 0);
+  }
+  polydet_plan_s *hit = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {  // a known shape: copy its template, share its tables
+      PlanTables *t = it->second;
+      ++t->refs;
+      t->last_use = ++g_cache_clock;
+      hit = new polydet_plan_s(*t->tmpl);
+      hit->tables = t;
+      hit->d_status = nullptr;
+      hit->status_shared = 1;
+    }
+  }
+  if (hit) return finish_plan(hit, shared_status, out);  // outside the lock: it may free the plan
 
   polydet_plan_s *pl = new polydet_plan_s();
   memset(pl, 0, sizeof *pl);
@@ -547,32 +645,62 @@ static int plan_impl(polydet_plan_t *out, int n, int nvars, const int32_t *entry
   pl->eval_ws_words = eval_slot * (uint64_t)n2;
   pl->interp_ws_words = 2 * interp_slot;
 
-  int rc;
-  if ((rc = upload(&pl->d_mod, mod)) || (rc = upload(&pl->d_tw_fwd, twf)) ||
-      (rc = upload(&pl->d_tw_inv, twi)) || (rc = upload(&pl->d_ninv, ninv)) ||
-      (rc = upload(&pl->d_rn, rn)) || (rc = upload(&pl->d_garner, garner)) ||
-      (rc = upload(&pl->d_mhalf, H)) || (rc = upload(&pl->d_mfull, M)) ||
-      (rc = upload(&pl->d_status, std::vector<uint32_t>(1, 0u))) ||
-      (!pl->full && (rc = upload(&pl->d_itab, itab)))) {
-    free_plan(pl);
-    return rc;
+  // one packed block for every table; the plan becomes the shape's template
+  Packer pk;
+  const size_t o_mod = pk.add(mod), o_twf = pk.add(twf), o_twi = pk.add(twi), o_ninv = pk.add(ninv),
+               o_rn = pk.add(rn), o_gar = pk.add(garner), o_mh = pk.add(H), o_mf = pk.add(M),
+               o_itab = pk.add(itab);
+  void *dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, pk.host.size());
+  if (e != cudaSuccess) {
+    pd_set_error("cudaMalloc", e);
+    delete pl;
+    return POLYDET_ENOMEM;
   }
-  for (int e = 0; e < n * n; ++e) pl->ent[e] = e;
+  e = cudaMemcpy(dev, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    pd_set_error("cudaMemcpy", e);
+    cudaFree(dev);
+    delete pl;
+    return POLYDET_ECUDA;
+  }
+  uint8_t *b = static_cast<uint8_t *>(dev);
+  pl->d_mod = reinterpret_cast<ModP *>(b + o_mod);
+  pl->d_tw_fwd = reinterpret_cast<uint32_t *>(b + o_twf);
+  pl->d_tw_inv = reinterpret_cast<uint32_t *>(b + o_twi);
+  pl->d_ninv = reinterpret_cast<uint32_t *>(b + o_ninv);
+  pl->d_rn = reinterpret_cast<uint32_t *>(b + o_rn);
+  pl->d_garner = reinterpret_cast<uint32_t *>(b + o_gar);
+  pl->d_mhalf = reinterpret_cast<uint32_t *>(b + o_mh);
+  pl->d_mfull = reinterpret_cast<uint32_t *>(b + o_mf);
+  pl->d_itab = pl->full ? nullptr : reinterpret_cast<uint32_t *>(b + o_itab);
+  for (int q = 0; q < n * n; ++q) pl->ent[q] = q;
   pl->nent = n * n;
   pl->nitems = n * n;
-  *out = pl;
-  return POLYDET_OK;
+  PlanTables *t = new PlanTables();
+  t->dev = dev;
+  t->tmpl = new polydet_plan_s(*pl);
+  {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    t->refs = 1;
+    t->last_use = ++g_cache_clock;
+    // a shape built concurrently by two threads: the first one stays cached,
+    // the other's tables go with its plan
+    t->cached = g_cache.emplace(key, t).second;
+  }
+  pl->tables = t;
+  return finish_plan(pl, shared_status, out);
 }
 
 extern "C" int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
                             int nprimes, uint32_t flags) {
-  return plan_impl(out, n, nvars, entry_deg, nullptr, nprimes, flags);
+  return pd_plan_impl(out, n, nvars, entry_deg, nullptr, nprimes, flags, nullptr);
 }
 
 extern "C" int polydet_plan_degrees(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,
                                     const int32_t *det_deg, int nprimes, uint32_t flags) {
   if (!det_deg) return POLYDET_EINVAL;
-  return plan_impl(out, n, nvars, entry_deg, det_deg, nprimes, flags);
+  return pd_plan_impl(out, n, nvars, entry_deg, det_deg, nprimes, flags, nullptr);
 }
 
 extern "C" int polydet_plan_set_entry_map(polydet_plan_t pl, const int32_t *map, int U) {

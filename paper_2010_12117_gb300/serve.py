@@ -179,7 +179,8 @@ class Server:
                     slot = free_slots.pop()
                     st = self.streams[slot]
                     start = time.perf_counter() - t0
-                    runner = BatchedRunner([arrivals[j].job for j in wave], tune="cache", stream=st)
+                    runner = BatchedRunner([arrivals[j].job for j in wave], nprimes=[shapes[j].P for j in wave],
+                                           tune="cache", stream=st)
                     runner.upload(st)
                     runner.compute(st)
                     runner.download(st)
