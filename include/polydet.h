@@ -277,6 +277,26 @@ int polydet_interp_static(polydet_plan_t plan, const uint32_t *detvals_dev, int 
 int polydet_crt(polydet_plan_t plan, const uint32_t *residues_dev, uint32_t *limbs_dev,
                 void *stream);
 
+/* Early termination (no counterpart in the paper: it stops adding primes
+ * once the reconstruction stops changing, instead of always using the prime
+ * count of the coefficient bound).  After primes 0 .. i of a plan (i >= 1,
+ * i < P) have their residues, computes the mixed-radix (Garner) digit i of
+ * every coefficient and ORs 1 into device word *unstable_dev if for some
+ * coefficient the symmetric lift of its residues over the first i primes
+ * differs from the lift over the first i + 1 (i.e. digit i is not 0 for a
+ * value in the lower half of [0, M_i), nor p_i - 1 for one in the upper
+ * half).  residues_dev: device uint32 [P][C] (primes 0 .. i valid);
+ * digits_dev: device uint32 [P][C], digits 0 .. i - 1 as left by the calls
+ * for 1 .. i - 1 (the call for i = 1 also writes digit 0); the caller clears
+ * *unstable_dev.  When a call leaves it 0, every coefficient is already
+ * determined by i primes unless, for each coefficient still wrong, p_i
+ * divides (true value - lift) / M_i: with the check prime regarded as
+ * random among the table primes not yet used, a chance of at most
+ * log2(2 B / M_i) / 30 over their number for a bound B on the coefficients.
+ * The caller then takes the CRT over the first i + 1 primes. */
+int polydet_crt_check(polydet_plan_t plan, const uint32_t *residues_dev, uint32_t *digits_dev,
+                      int i, uint32_t *unstable_dev, void *stream);
+
 /* Synchronise `stream`, return the plan's status word in *status_out and clear
  * it.  Returns POLYDET_EBOUND / POLYDET_ETIMEOUT if the matching bit was set. */
 int polydet_sync_status(polydet_plan_t plan, void *stream, uint32_t *status_out);

@@ -297,3 +297,13 @@ def count_ntt_primes_after(start: int, count: int, qs: Sequence[int]) -> Dict[in
                 if (p - 1) % (1 << q) == 0:
                     out[q] += 1
     return out
+
+
+def lift_is_stable(xs: Sequence[int], primes: Sequence[int]) -> bool:
+    """Early termination's test, by its plain definition: the symmetric lift
+    of the residues ``xs[:i]`` over the first i primes equals the symmetric
+    lift of ``xs[:i + 1]`` over the first i + 1 (i = len(xs) - 1 >= 1)."""
+    i = len(xs) - 1
+    a = symmetric_lift(crt_direct(xs[:i], primes[:i]), prod(primes[:i]))
+    b = symmetric_lift(crt_direct(xs, primes[:i + 1]), prod(primes[:i + 1]))
+    return a == b

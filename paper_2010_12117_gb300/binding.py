@@ -96,6 +96,7 @@ SIGNATURES = {
     "polydet_interp": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP]),
     "polydet_interp_static": (_I, [_VP, _VP, _I, _I, _VP, _VP]),
     "polydet_crt": (_I, [_VP, _VP, _VP, _VP]),
+    "polydet_crt_check": (_I, [_VP, _VP, _VP, _I, _VP, _VP]),
     "polydet_sync_status": (_I, [_VP, _VP, _PU32]),
     "polydet_batch_plan": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(Job), _I, _U32]),
     "polydet_batch_destroy": (_I, [_VP]),
@@ -374,6 +375,15 @@ class Plan:
         _check(lib().polydet_crt(self._h, _ptr(residues, torch.int32, self.P * self.C, "residues"),
                                  _ptr(limbs, torch.int32, self.C * self.W, "limbs"), _stream(stream)),
                "polydet_crt")
+
+    def crt_check(self, residues: torch.Tensor, digits: torch.Tensor, i: int, unstable: torch.Tensor,
+                  stream=None) -> None:
+        """Digit i of every coefficient; ORs 1 into ``unstable`` when the
+        reconstruction from i primes is changed by prime i (early stop)."""
+        _check(lib().polydet_crt_check(self._h, _ptr(residues, torch.int32, (i + 1) * self.C, "residues"),
+                                       _ptr(digits, torch.int32, (i + 1) * self.C, "digits"), int(i),
+                                       _ptr(unstable, torch.int32, 1, "unstable"), _stream(stream)),
+               "polydet_crt_check")
 
     def sync_status(self, stream=None) -> int:
         st = ctypes.c_uint32(0)

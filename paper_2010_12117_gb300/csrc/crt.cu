@@ -217,3 +217,53 @@ extern "C" int polydet_crt(polydet_plan_t pl, const uint32_t *residues, uint32_t
   PD_CUDA(cudaGetLastError());
   return POLYDET_OK;
 }
+
+// Early termination (no counterpart in the paper): digit i of every
+// coefficient, from the stored digits 0 .. i-1, and whether the symmetric
+// reconstruction from the first i primes survives prime i.  With
+// X_i = sum_{j<i} alpha_j prod_{l<j} p_l in [0, M_i), the symmetric lift is
+// X_i itself when X_i <= (M_i - 1) / 2 and X_i - M_i otherwise; it is also
+// the lift over M_{i+1} exactly when alpha_i = 0 (first case) or
+// alpha_i = p_i - 1 (second case).  The mixed-radix digits of (M_i - 1) / 2
+// are (p_j - 1) / 2 for every j (the sum telescopes), so the comparison of
+// X_i with it runs over the digits from the top.
+__global__ void __launch_bounds__(256) crt_check_kernel(const uint32_t *__restrict__ res,
+                                                        uint32_t *__restrict__ digits, int64_t C,
+                                                        int P, int i, const ModP *__restrict__ mod,
+                                                        const uint32_t *__restrict__ garner,
+                                                        uint32_t *__restrict__ unstable) {
+  const ModP m = mod[i];
+  bool bad = false;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    if (i == 1) digits[c] = res[c];  // alpha_0 = x_0
+    uint32_t acc = 0u;
+    int cmp = 0;  // X_i against (M_i - 1) / 2, decided by the highest differing digit
+    for (int j = i - 1; j >= 0; --j) {
+      const uint32_t a = digits[(int64_t)j * C + c];
+      acc = addm(acc, mmul(a, __ldg(garner + i * P + j), m.p, m.pinv), m.p);
+      const uint32_t h = (mod[j].p - 1u) >> 1;
+      if (cmp == 0) cmp = (a > h) ? 1 : ((a < h) ? -1 : 0);
+    }
+    const uint32_t x = res[(int64_t)i * C + c];
+    const uint32_t ai = mmul(subm(x, acc, m.p), __ldg(garner + i * P + i), m.p, m.pinv);
+    digits[(int64_t)i * C + c] = ai;
+    bad |= (cmp > 0) ? (ai != m.p - 1u) : (ai != 0u);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(unstable, 1u);
+}
+
+extern "C" int polydet_crt_check(polydet_plan_t pl, const uint32_t *residues, uint32_t *digits,
+                                 int i, uint32_t *unstable, void *stream) {
+  if (!pl || !residues || !digits || !unstable || i < 1 || i >= pl->P) return POLYDET_EINVAL;
+  int dev = 0, sms = 0;
+  PD_CUDA(cudaGetDevice(&dev));
+  PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int threads = 256;
+  const int64_t want = (pl->C + threads - 1) / threads;
+  const unsigned blocks = (unsigned)(want < (int64_t)sms * 16 ? want : (int64_t)sms * 16);
+  crt_check_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(residues, digits, pl->C, pl->P, i,
+                                                                 pl->d_mod, pl->d_garner, unstable);
+  PD_CUDA(cudaGetLastError());
+  return POLYDET_OK;
+}

@@ -28,6 +28,7 @@ class DetResult:
     P: int
     W: int
     limbs: np.ndarray      # [C][W] uint32
+    primes_bound: int = -1  # primes of the coefficient bound (P is fewer after an early stop)
 
 
 def unpermute_output(vals: Sequence[int], order: Sequence[int], box: Sequence[int]) -> List[int]:
@@ -69,7 +70,8 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
                 stream: Optional[torch.cuda.Stream] = None,
                 stop_after_chunks: Optional[int] = None, full_grid: bool = False,
                 tight_degrees: bool = False, unique_entries: bool = False,
-                streamed: Optional[bool] = None, as_ints: bool = True) -> DetResult:
+                streamed: Optional[bool] = None, as_ints: bool = True,
+                early_stop: bool = False) -> DetResult:
     """Exact det of the polynomial matrix ``coeffs`` [n][n][E] (lex encoding
     of Sec. 2) with entry degrees ``degs``; returns its coefficients over the
     box prod [0, D_v].
@@ -82,7 +84,10 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
     variable of lowest degree taken first (its nodes are the slabs); None
     streams exactly when one prime's evaluated matrices exceed the budget.
     ``as_ints``: False leaves ``coeffs`` None (outputs of hundreds of
-    millions of coefficients are read from ``limbs``)."""
+    millions of coefficients are read from ``limbs``).  ``early_stop``:
+    primes one at a time, and stop at the first prime that leaves every
+    coefficient's reconstruction unchanged (polydet_crt_check); P is then
+    the primes used, ``primes_bound`` the count of the coefficient bound."""
     coeffs = np.asarray(coeffs)
     n = coeffs.shape[0]
     if coeffs.shape[:2] != (n, n):
@@ -112,7 +117,7 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
         return determinant(coeffs, degs, nprimes=P, store=store, budget_bytes=budget_bytes,
                            stream=stream, stop_after_chunks=stop_after_chunks, full_grid=full_grid,
                            tight_degrees=tight_degrees, unique_entries=unique_entries, streamed=False,
-                           as_ints=as_ints)
+                           as_ints=as_ints, early_stop=early_stop)
     dev = torch.device("cuda")
     st = stream if stream is not None else torch.cuda.current_stream()
     with torch.cuda.stream(st):
@@ -127,6 +132,8 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
             for q, r in store.done(P, plan.C).items():
                 residues[q * plan.C:(q + 1) * plan.C].copy_(torch.from_numpy(r.view(np.int32)))
                 todo.remove(q)
+        if early_stop and store is not None:
+            raise ValueError("early_stop and a residue store do not combine")
         if streamed:
             ch = 1
             ws_words = max(plan.stream_ws_words(1), plan.interp_ws_words,
@@ -134,7 +141,7 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
             evals = None
             ws = torch.empty(ws_words, dtype=torch.int32, device=dev) if todo else None
         else:
-            ch = _chunk(plan, budget_bytes)
+            ch = 1 if early_stop else _chunk(plan, budget_bytes)
             evals = torch.empty(ch * plan.entries * plan.G, dtype=torch.int32, device=dev) if todo else None
             ws = plan.workspace(ch) if todo else None
         detv = torch.empty(ch * plan.G, dtype=torch.int32, device=dev) if todo else None
@@ -144,6 +151,10 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
                 runs[-1][1] = q + 1
             else:
                 runs.append([q, q + 1])
+        used = P
+        if early_stop:
+            digits = torch.empty(P * plan.C, dtype=torch.int32, device=dev)
+            unstable = torch.zeros(1, dtype=torch.int32, device=dev)
         for done, (lo, hi) in enumerate(runs):
             if stop_after_chunks is not None and done >= stop_after_chunks:
                 raise InterruptedError("stopped after the requested number of chunks")
@@ -163,15 +174,25 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
                 host = as_u32(residues[lo * plan.C:hi * plan.C])
                 for q in range(lo, hi):
                     store.save(q, host[(q - lo) * plan.C:(q - lo + 1) * plan.C])
+            if early_stop and lo >= 1:
+                plan.crt_check(residues, digits, lo, unstable, st)
+                if int(unstable.item()) == 0:  # prime lo changed no coefficient: stop
+                    used = lo + 1
+                    break
+                unstable.zero_()
         del evals, ws, detv
-        limbs = torch.empty(plan.C * plan.W, dtype=torch.int32, device=dev)
-        plan.crt(residues, limbs, st)
+        cplan = plan if used == P else Plan(n, dp, used, full_grid=full_grid, det_degs=D)
+        limbs = torch.empty(cplan.C * cplan.W, dtype=torch.int32, device=dev)
+        cplan.crt(residues, limbs, st)
         status = plan.sync_status(st)
         if status:
             raise PolydetError(EBOUND, f"device status {status:#x}")
-        host_limbs = as_u32(limbs).reshape(plan.C, plan.W)
+        host_limbs = as_u32(limbs).reshape(cplan.C, cplan.W)
+        W = cplan.W
+        if cplan is not plan:
+            cplan.close()
     box = tuple(int(x) + 1 for x in plan.D)
-    vals = limbs_to_ints(host_limbs, plan.W) if as_ints else None
+    vals = limbs_to_ints(host_limbs, W) if as_ints else None
     Dc = [0] * len(degs)
     for i, v in enumerate(order):
         Dc[v] = plan.D[i]
@@ -179,7 +200,7 @@ def determinant(coeffs: np.ndarray, degs: Sequence[int], nprimes: Optional[int] 
         if as_ints:
             vals = unpermute_output(vals, order, box)
         inv = [order.index(v) for v in range(len(order))]
-        host_limbs = host_limbs.reshape(box + (plan.W,)).transpose(tuple(inv) + (len(order),)).reshape(-1, plan.W)
-    out = DetResult(vals, tuple(Dc), plan.P, plan.W, np.ascontiguousarray(host_limbs))
+        host_limbs = host_limbs.reshape(box + (W,)).transpose(tuple(inv) + (len(order),)).reshape(-1, W)
+    out = DetResult(vals, tuple(Dc), used, W, np.ascontiguousarray(host_limbs), primes_bound=P)
     plan.close()
     return out

@@ -58,10 +58,10 @@ class ServeReport:
     failed: int = 0  # jobs of waves whose device status word was set
 
     def summary(self) -> dict:
-        return {"jobs": self.jobs, "waves": self.waves, "wall_s": self.wall_s,
-                "p50_ms": self.p50_ms, "p99_ms": self.p99_ms, "mean_ms": self.mean_ms,
-                "exact_dets_per_s": self.exact_dets_per_s, "modp_dets": self.modp_dets,
-                "peak_predicted_mem_bytes": self.peak_pred_mem, "failed_jobs": self.failed}
+        return {"jobs": int(self.jobs), "waves": int(self.waves), "wall_s": float(self.wall_s),
+                "p50_ms": float(self.p50_ms), "p99_ms": float(self.p99_ms), "mean_ms": float(self.mean_ms),
+                "exact_dets_per_s": float(self.exact_dets_per_s), "modp_dets": int(self.modp_dets),
+                "peak_predicted_mem_bytes": float(self.peak_pred_mem), "failed_jobs": int(self.failed)}
 
 
 def measure(pm, stream: torch.cuda.Stream, reps: int = 2) -> tuple:

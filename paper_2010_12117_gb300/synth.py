@@ -16,6 +16,7 @@ Draw order (numpy ``default_rng(seed)``, PCG64), per workload:
 * ``sylvester_16``: f then g, each ``integers(-2**15, 2**15, (9, 7))`` indexed
   [power of y][power of x]; the 16x16 Sylvester matrix in y is then laid out.
 * ``sylvester`` / ``sylvester_15_four_vars``: see ``sylvester``.
+* ``small_det_matrix``: see its docstring.
 * ``sparse_12x12_xyz``: ``random((12, 12, 64)) < 0.3`` (monomial mask) then
   ``integers(-128, 128, (12, 12, 64))`` (values); masked-out values become 0.
 * ``batched``: per matrix, in order: n = integers(4, 25); k = integers(1, 4);
@@ -150,6 +151,39 @@ def sylvester_15_four_vars(seed: int, density: float = 0.01) -> PolyMatrix:
     pm = sylvester(rng, 8, 7, (22, 13, 9, 3), (18, 10, 7, 3), density, -128, 128)
     pm.name = f"sylvester_15_x1x2x3x4/seed{seed}"
     return pm
+
+
+def small_det_matrix(rng: np.random.Generator, n: int, degs: Sequence[int], diag_degs: Sequence[int],
+                     mixes: int = 0) -> PolyMatrix:
+    """An n x n matrix over Z[x1..xk] whose determinant is far smaller than
+    its Hadamard bound.  Draws, in order: entries strictly above the diagonal
+    dense int16 over the box ``degs``; diagonal entries over the box
+    ``diag_degs`` with coefficients in [-2, 2] and a constant term in {1, 2}
+    (entries below the diagonal are zero); then ``mixes`` integer row
+    operations row_i += c row_j (i != j, c in [-3, 3]) and a random
+    permutation of the rows and one of the columns.  The determinant is,
+    up to sign, the product of the diagonal entries drawn."""
+    degs = tuple(int(d) for d in degs)
+    shape = tuple(d + 1 for d in degs)
+    E = int(np.prod(shape))
+    c = np.zeros((n, n, E), dtype=np.int64)
+    for i in range(n):
+        for j in range(i + 1, n):
+            c[i, j] = rng.integers(INT16_LO, INT16_HI, E)
+    for i in range(n):
+        dsh = tuple(int(d) + 1 for d in diag_degs)
+        d = rng.integers(-2, 3, dsh)
+        d.flat[0] = int(rng.integers(1, 3))
+        box = np.zeros(shape, dtype=np.int64)
+        box[tuple(slice(0, k) for k in dsh)] = d
+        c[i, i] = box.reshape(-1)
+    for _ in range(mixes):
+        i, j = (int(x) for x in rng.choice(n, 2, replace=False))
+        c[i] += int(rng.integers(-3, 4)) * c[j]
+    c = c[rng.permutation(n)][:, rng.permutation(n)]
+    if np.abs(c).max() >= 2 ** 31:
+        raise ValueError("mixed entries no longer fit in int32")
+    return PolyMatrix(n, degs, c, name=f"small_det_{n}x{n}_k{len(degs)}")
 
 
 def sylvester_16(seed: int) -> PolyMatrix:

@@ -643,3 +643,25 @@ def test_check_limbs_accepts_truth_and_rejects_planted_errors():
         bad = L.copy()
         bad[j, int(rng.integers(0, W))] ^= np.uint32(1 << int(rng.integers(0, 32)))
         assert not certificate.check_limbs(pm.coeffs, pm.degs, bad, D, trials=2)
+
+
+def test_lift_stability_by_value():
+    """The symmetric lift over i primes is unchanged by prime i exactly for
+    values with |v| <= (M_i - 1) / 2 (both lifts are v); for values between
+    that and (M_{i+1} - 1) / 2 it changes."""
+    from math import prod as _prod
+    ps = PRIMES[:6]
+    rng = np.random.default_rng(61)
+    for i in range(1, 6):
+        Mi, Mn = _prod(ps[:i]), _prod(ps[:i + 1])
+        small = [0, 1, -1, (Mi - 1) // 2, -((Mi - 1) // 2)] + [int(x) for x in rng.integers(-(Mi // 2), Mi // 2, 5)] \
+            if Mi < 2 ** 62 else [0, 1, -1, (Mi - 1) // 2, -((Mi - 1) // 2)]
+        large = [(Mi + 1) // 2, -((Mi + 1) // 2), (Mn - 1) // 2, -((Mn - 1) // 2), Mi, -Mi, 3 * Mi + 7]
+        for v in small:
+            assert modular.lift_is_stable([v % p for p in ps[:i + 1]], ps), (i, v)
+        for v in large:
+            assert not modular.lift_is_stable([v % p for p in ps[:i + 1]], ps), (i, v)
+    # the mixed-radix digits of (M - 1) / 2 are (p_j - 1) / 2
+    for i in range(1, 7):
+        h = (_prod(PRIMES[:i]) - 1) // 2
+        assert modular.mixed_radix_digits([h % p for p in PRIMES[:i]], PRIMES[:i]) == [(p - 1) // 2 for p in PRIMES[:i]]
