@@ -80,7 +80,6 @@ template <int PT>
 struct CrtTab {
   uint32_t gs[PT * PT];  // see polydet_plan_s::crt_gs
   uint32_t p[PT], pinv[PT];
-  uint32_t mh[PT], mf[PT];  // (M - 1) / 2 and M, limbs (zero above W)
 };
 
 template <int PT>
@@ -112,21 +111,38 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
       for (int i = 0; i < PT; ++i, rp += C) xn[i] = __ldg(rp);
     }
     // Garner digits (Sec. 3.4): alpha_i = x_i c_i - sum_{j<i} alpha_j m_j c_i
-    // mod p_i as one dot product; two 62-bit products (each below 2^31 p_i)
-    // share one REDC
+    // mod p_i as one dot product; three 62-bit products share one REDC (every
+    // prime of a plan of at most 32 is at most PD_FOLD3_MAX, see redc3)
     al[0] = x[0];
 #pragma unroll
     for (int i = 1; i < PT; ++i) {
       const uint32_t p = tab.p[i], pinv = tab.pinv[i];
       uint32_t acc = 0u;
 #pragma unroll
-      for (int j = 0; j <= i; j += 2) {
+      for (int j = 0; j <= i; j += 3) {
         uint64_t sum = (uint64_t)(j < i ? al[j] : x[i]) * tab.gs[i * PT + j];
         if (j + 1 <= i) sum += (uint64_t)(j + 1 < i ? al[j + 1] : x[i]) * tab.gs[i * PT + j + 1];
-        acc = (j == 0) ? redc(sum, p, pinv) : addm(acc, redc(sum, p, pinv), p);
+        if (j + 2 <= i) sum += (uint64_t)(j + 2 < i ? al[j + 2] : x[i]) * tab.gs[i * PT + j + 2];
+        const uint32_t r = (j + 2 <= i) ? redc3(sum, p, pinv) : redc(sum, p, pinv);
+        acc = (j == 0) ? r : addm(acc, r, p);
       }
       al[i] = acc;
     }
+    // symmetric lift from the digits: X > (M - 1) / 2 exactly when the digit
+    // vector, read from the top, first differs from that of (M - 1) / 2, whose
+    // digits are (p_j - 1) / 2, by exceeding it.  Then X - M = -(Y + 1) with
+    // Y = M - 1 - X, whose digits are p_j - 1 - alpha_j: Horner on those
+    // digits and the bitwise complement of the words give X - M in two's
+    // complement.
+    int cmp = 0;
+#pragma unroll
+    for (int i = PT - 1; i >= 0; --i) {
+      const uint32_t h = (tab.p[i] - 1u) >> 1;
+      if (cmp == 0) cmp = (al[i] > h) ? 1 : ((al[i] < h) ? -1 : 0);
+    }
+    const bool neg = cmp > 0;
+#pragma unroll
+    for (int i = 0; i < PT; ++i) al[i] = neg ? tab.p[i] - 1u - al[i] : al[i];
     // mixed radix to binary by Horner: X = (..(alpha_{P-1} p_{P-2} + alpha_{P-2}) ..) p_0 + alpha_0
     uint32_t X[PT];
 #pragma unroll
@@ -143,23 +159,9 @@ __global__ void __launch_bounds__(256) crt_kernel_p(const uint32_t *__restrict__
         carry = t >> 32;
       }
     }
-    // symmetric lift: X > (M - 1) / 2 becomes X - M (two's complement)
-    int cmp = 0;
-#pragma unroll
-    for (int w = PT - 1; w >= 0; --w)
-      if (cmp == 0 && w < W) cmp = (X[w] > tab.mh[w]) ? 1 : ((X[w] < tab.mh[w]) ? -1 : 0);
-    if (cmp > 0) {
-      uint32_t borrow = 0u;
-#pragma unroll
-      for (int w = 0; w < PT; ++w) {
-        const uint64_t t = (uint64_t)X[w] - tab.mf[w] - borrow;
-        X[w] = (uint32_t)t;
-        borrow = (uint32_t)(t >> 63);
-      }
-    }
 #pragma unroll
     for (int w = 0; w < PT; ++w)
-      if (w < W) sw[lane * W + w] = X[w];
+      if (w < W) sw[lane * W + w] = neg ? ~X[w] : X[w];
     __syncwarp();
     const int nw = (C - c0 < 32 ? (int)(C - c0) : 32) * W;  // words of this warp's coefficients
     uint32_t *o = limbs + c0 * W;
@@ -184,8 +186,6 @@ static int launch_crt_p(const polydet_plan_s *pl, const uint32_t *residues, uint
     for (int i = 0; i < PT; ++i) {
       tab.p[i] = pl->mod_h[i].p;
       tab.pinv[i] = pl->mod_h[i].pinv;
-      tab.mh[i] = i < pl->W ? pl->crt_mh[i] : 0u;
-      tab.mf[i] = i < pl->W ? pl->crt_mf[i] : 0u;
     }
     const int threads = 256;
     const int64_t want = (pl->C + threads - 1) / threads;

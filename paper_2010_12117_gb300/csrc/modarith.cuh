@@ -46,18 +46,22 @@ PD_D uint32_t mfms(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t p,
 // [0, p) exactly when r_max + p < 2^32 and r_max < 2p.
 #define PD_FOLD3_MAX 1865126253u
 
-// (a*b + c*d + e*f) / R mod p for all six operands in [0, p) and
-// p <= PD_FOLD3_MAX: the sum stays below 3 p^2 < 2^64, one REDC leaves
-// r in (-p, r_max] (an interval shorter than 2^32, so no two values share a
-// 32-bit pattern); min(r, r + p) folds the wrapped negatives into [0, p),
-// then min(r, r - p) folds [p, r_max] (r_max < 2p) into [0, p).
-PD_D uint32_t mfms3(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e, uint32_t f,
-                    uint32_t p, uint32_t pinv) {
-  const uint64_t x = (uint64_t)a * b + (uint64_t)c * d + (uint64_t)e * f;
+// x / R mod p for x < 3 p^2 (a sum of up to three products of residues) and
+// p <= PD_FOLD3_MAX: one REDC leaves r in (-p, r_max] (an interval shorter
+// than 2^32, so no two values share a 32-bit pattern); min(r, r + p) folds
+// the wrapped negatives into [0, p), then min(r, r - p) folds [p, r_max]
+// (r_max < 2p) into [0, p).  mfms3: (a*b + c*d + e*f) / R mod p for all six
+// operands in [0, p).
+PD_D uint32_t redc3(uint64_t x, uint32_t p, uint32_t pinv) {  // x < 3 p^2, p <= PD_FOLD3_MAX
   const uint32_t m = (uint32_t)x * pinv;
   uint32_t r = (uint32_t)(x >> 32) - __umulhi(m, p);
   r = min(r, r + p);
   return min(r, r - p);
+}
+
+PD_D uint32_t mfms3(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e, uint32_t f,
+                    uint32_t p, uint32_t pinv) {
+  return redc3((uint64_t)a * b + (uint64_t)c * d + (uint64_t)e * f, p, pinv);
 }
 
 PD_D uint32_t addm(uint32_t a, uint32_t b, uint32_t p) {

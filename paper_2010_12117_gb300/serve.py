@@ -5,7 +5,9 @@ Requests arrive over time (seeded Poisson stream).  The loop keeps up to
 free it forms a wave from the requests that have arrived - shortest predicted
 run time first, requests that have waited longest jumped ahead - admitting
 while the predicted device memory of everything in flight stays within the
-budget and the wave's predicted time stays within ``wave_seconds``.  A wave
+budget and the wave's predicted time stays within ``wave_seconds`` (up to
+``backlog_factor`` times that while the queue holds more predicted work than
+the slots can start at the target).  A wave
 is one batched run (fused kernels, no host synchronisation inside); its limbs
 come back asynchronously and the loop notices completion through an event.
 Freed buffers go back to torch's stream-ordered caching allocator, so a
@@ -102,13 +104,15 @@ def calibrate(mats: Sequence, stream: Optional[torch.cuda.Stream] = None, reps: 
 
 class Server:
     def __init__(self, predictor: Optional[Predictor], mem_budget: float, slots: int = 2,
-                 wave_seconds: float = 0.05, max_wave_jobs: int = 64, max_wait: float = 0.25):
+                 wave_seconds: float = 0.05, max_wave_jobs: int = 128, max_wait: float = 0.25,
+                 backlog_factor: float = 4.0):
         self.pred = predictor or Predictor()
         self.mem_budget = float(mem_budget)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.wave_seconds = wave_seconds
         self.max_wave_jobs = max_wave_jobs
         self.max_wait = max_wait
+        self.backlog_factor = backlog_factor
 
     def run(self, arrivals: Sequence, keep_results: bool = True) -> ServeReport:
         shapes: List[Shape] = [shape_of(a.job) for a in arrivals]
@@ -162,6 +166,14 @@ class Server:
                 now = time.perf_counter() - t0
                 waiting = sorted(pending, key=lambda j: (0 if now - arrivals[j].t > self.max_wait else 1,
                                                          preds[j][0]))
+                # a backlog larger than the slots can start at the wave target
+                # gets waves up to backlog_factor times longer (fewer, larger
+                # batched runs: more jobs per launch), sized so that the slots
+                # share it
+                backlog = float(sum(preds[j][0] for j in pending))
+                limit = self.wave_seconds
+                if backlog > self.wave_seconds * len(self.streams):
+                    limit = min(self.backlog_factor * self.wave_seconds, backlog / len(self.streams))
                 wave, wt, wm = [], 0.0, 0.0
                 for j in waiting:
                     if len(wave) >= self.max_wave_jobs:
@@ -169,7 +181,7 @@ class Server:
                     t_j, m_j = preds[j]
                     fits_mem = mem_used + wm + m_j <= self.mem_budget
                     alone = not wave and not inflight  # too big for the budget: run it by itself
-                    if (fits_mem or alone) and (not wave or wt + t_j <= self.wave_seconds):
+                    if (fits_mem or alone) and (not wave or wt + t_j <= limit):
                         wave.append(j)
                         wt += t_j
                         wm += m_j
