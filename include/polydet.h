@@ -395,6 +395,12 @@ int polydet_batch_set_launch(polydet_batch_t batch, int n, int threads);
  * content and the workspace size (query again); rerun polydet_batch_eval
  * before the next condense.  Not during a graph capture. */
 int polydet_batch_set_mode(polydet_batch_t batch, int n, int mode);
+/* Materialized mode: at most `ctas_per_sm` CTAs of the condensation kernel
+ * per SM (0, the default: as many as its registers allow; 1..16 reserve
+ * shared memory the kernel does not use so that no more fit), which leaves
+ * registers for the first-variable passes to run beside the condensation
+ * instead of waiting for it. */
+int polydet_batch_set_condense_ctas(polydet_batch_t batch, int ctas_per_sm);
 /* Chunk budget of the materialized mode in words (>= 1; the workspace size
  * changes: query again).  Not during a graph capture. */
 int polydet_batch_set_chunk_words(polydet_batch_t batch, uint64_t words);

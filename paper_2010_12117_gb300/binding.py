@@ -106,6 +106,7 @@ SIGNATURES = {
     "polydet_batch_set_launch": (_I, [_VP, _I, _I]),
     "polydet_batch_set_mode": (_I, [_VP, _I, _I]),
     "polydet_batch_set_chunk_words": (_I, [_VP, ctypes.c_uint64]),
+    "polydet_batch_set_condense_ctas": (_I, [_VP, _I]),
     "polydet_team_size": (_I, [_I]),
     "polydet_batch_test_drop_copies": (_I, [_VP, _I]),
     "polydet_batch_eval": (_I, [_VP, _VP, _VP, _VP, _VP]),
@@ -472,6 +473,12 @@ class Batch:
         """Budget (words) of one materialized chunk; at least one prime."""
         _check(lib().polydet_batch_set_chunk_words(self._h, int(words)), "polydet_batch_set_chunk_words")
         self.refresh()
+
+    def set_condense_ctas(self, ctas_per_sm: int) -> None:
+        """Cap the materialized orders' condensation at this many CTAs per SM
+        (0: no cap) so that the first-variable passes run beside it."""
+        _check(lib().polydet_batch_set_condense_ctas(self._h, int(ctas_per_sm)),
+               "polydet_batch_set_condense_ctas")
 
     def test_drop_copies(self, on: bool) -> None:
         """Failure-detection test hook: withhold the fused kernels' bulk

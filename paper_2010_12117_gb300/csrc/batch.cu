@@ -145,6 +145,9 @@ struct polydet_batch_s {
   // it), so that reading the batch's status is one copy, not one per job
   uint32_t *d_status = nullptr;
   BatchRes *res = nullptr;  // the pooled set the pointers above come from
+  // materialized orders: condensation CTAs per SM (0: as many as registers
+  // allow), so that the first-variable passes find room beside them
+  int condense_ctas = 0;
 };
 
 static int fan_begin(polydet_batch_s *b, cudaStream_t st) {
@@ -420,6 +423,12 @@ extern "C" int polydet_batch_set_mode(polydet_batch_t b, int n, int mode) {
   return POLYDET_OK;
 }
 
+extern "C" int polydet_batch_set_condense_ctas(polydet_batch_t b, int ctas_per_sm) {
+  if (!b || ctas_per_sm < 0 || ctas_per_sm > 16) return POLYDET_EINVAL;
+  b->condense_ctas = ctas_per_sm;
+  return POLYDET_OK;
+}
+
 extern "C" int polydet_batch_set_chunk_words(polydet_batch_t b, uint64_t words) {
   if (!b || words < 1) return POLYDET_EINVAL;
   b->chunk_words = words;
@@ -505,7 +514,7 @@ static int condense_materialized(polydet_batch_s *b, int n, const uint32_t *part
       PD_CUDA(cudaEventRecord(b->ev[buf], sd));
       PD_CUDA(cudaStreamWaitEvent(st, b->ev[buf], 0));
       rc = pd_launch_condense(pl, chunk, lay, lo, hi - lo, detvals + b->det_off[j] + (int64_t)lo * pl->G,
-                              st);
+                              st, b->condense_ctas);
       if (rc) return rc;
       PD_CUDA(cudaEventRecord(b->ev[2 + buf], st));
     }

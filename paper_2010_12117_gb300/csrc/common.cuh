@@ -124,13 +124,15 @@ int pd_once_per_device(PdPerDevice &pd, F &&set) {
 struct EvLayout {
   int64_t rowlen, rowstride, entry;
 };
+// ctas_per_sm > 0 caps the condensation kernel's residency at that many CTAs
+// per SM (reserved shared memory), leaving registers to kernels beside it.
 int pd_launch_condense(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay, int prime_lo,
-                       int nprimes, uint32_t *detvals, cudaStream_t st);
+                       int nprimes, uint32_t *detvals, cudaStream_t st, int ctas_per_sm = 0);
 // The same over G nodes per prime (a slab of the grid), determinants of prime
 // slot q at detvals + q * det_stride.
 int pd_launch_condense_nodes(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay, int64_t G,
                              int64_t det_stride, int prime_lo, int nprimes, uint32_t *detvals,
-                             cudaStream_t st);
+                             cudaStream_t st, int ctas_per_sm = 0);
 
 // Evaluation of every variable but the last (x_k), for the fused kernels:
 // out[q][row][entry][Lp] with row over prod_{v<k} M_v (lex) holding the

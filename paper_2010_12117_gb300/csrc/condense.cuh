@@ -10,7 +10,7 @@
 // array is a compile-time constant after unrolling, and there are no
 // barriers: the team talks through warp shuffles.
 //
-// Elimination is fraction free (the paper's update, Algorithm 3 step (3)):
+// Elimination is fraction free (the update of Algorithm 3):
 // at step c every column j > c of every row i > c becomes
 // a_cc * a_ij - a_ic * a_cj, evaluated with one Montgomery REDC of the two
 // 62-bit products.  Reading every stored value s as the Montgomery form of
@@ -205,6 +205,77 @@ struct EntryOff {
   int64_t o[NN * NN];
 };
 
+// Three elimination steps at once (columns c, c + 1, c + 2): with the
+// trailing matrix's leading 3 x 3 block A11 of determinant D3, its cofactors
+// cof_lk and Schur complement S, for i, j >= c + 3
+//   D3 S_ij = D3 a_ij + sum_k C_kj a_i,c+k,  C_kj = -sum_l cof_lk a_c+l,j
+// (adj(A11) = cof^T), and det(trailing) = D3 det(D3 S) / D3^m, m = n - c - 3.
+// Each element costs four products and one REDC (redc4, any p < 2^31) for
+// three steps; each column three REDCs of three products per triple of
+// steps.  Fewer than three steps left: Fast2Step finishes.  A zero D3 is
+// only recorded, as in Fast2Step.
+template <int NN, int T, int c>
+struct Fast3Step {
+  static constexpr int M = (NN + T - 1) / T;
+  static constexpr int S = ColLayout<NN, T>::S;
+  static PD_D uint32_t bcast(uint32_t v, int owner) {
+    return (T == 1) ? v : __shfl_sync(PD_FULL, v, owner, T);
+  }
+  static PD_D uint32_t neg(uint32_t v, uint32_t p) { return v ? p - v : 0u; }
+  static PD_D void run(uint32_t (&a)[M][NN], uint32_t p, uint32_t pinv, uint32_t &Q,
+                       uint32_t &den, bool &zero) {
+    if constexpr (NN - c < 3) {
+      Fast2Step<NN, T, c>::run(a, p, pinv, Q, den, zero);
+    } else {
+      constexpr int o0 = (c + S) % T, m0 = (c + S) / T;
+      constexpr int o1 = (c + 1 + S) % T, m1 = (c + 1 + S) / T;
+      constexpr int o2 = (c + 2 + S) % T, m2 = (c + 2 + S) / T;
+      // A11[k][l] = a_{c+k, c+l}: column c+l is held by owner o_l in slot m_l
+      const uint32_t a00 = bcast(a[m0][c], o0), a10 = bcast(a[m0][c + 1], o0), a20 = bcast(a[m0][c + 2], o0);
+      const uint32_t a01 = bcast(a[m1][c], o1), a11 = bcast(a[m1][c + 1], o1), a21 = bcast(a[m1][c + 2], o1);
+      const uint32_t a02 = bcast(a[m2][c], o2), a12 = bcast(a[m2][c + 1], o2), a22 = bcast(a[m2][c + 2], o2);
+      const uint32_t c00 = mfms(a11, a22, a12, a21, p, pinv), c01 = mfms(a12, a20, a10, a22, p, pinv),
+                     c02 = mfms(a10, a21, a11, a20, p, pinv);
+      const uint32_t c10 = mfms(a02, a21, a01, a22, p, pinv), c11 = mfms(a00, a22, a02, a20, p, pinv),
+                     c12 = mfms(a01, a20, a00, a21, p, pinv);
+      const uint32_t c20 = mfms(a01, a12, a02, a11, p, pinv), c21 = mfms(a02, a10, a00, a12, p, pinv),
+                     c22 = mfms(a00, a11, a01, a10, p, pinv);
+      const uint32_t d3 = redc4((uint64_t)a00 * c00 + (uint64_t)a01 * c01 + (uint64_t)a02 * c02, p, pinv);
+      zero |= (d3 == 0u);
+      const uint32_t q2 = mmul(Q, Q, p, pinv);
+      den = mmul(den, mmul(q2, Q, p, pinv), p, pinv);
+      Q = mmul(Q, d3, p, pinv);
+      if constexpr (c + 3 < NN) {
+        // C_kj = -(cof_0k v_0 + cof_1k v_1 + cof_2k v_2), v_l = a_{c+l, j}
+        const uint32_t n00 = neg(c00, p), n10 = neg(c10, p), n20 = neg(c20, p);
+        const uint32_t n01 = neg(c01, p), n11 = neg(c11, p), n21 = neg(c21, p);
+        const uint32_t n02 = neg(c02, p), n12 = neg(c12, p), n22 = neg(c22, p);
+        uint32_t k0[M], k1[M], k2[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          if (T * m + T - 1 - S > c + 2) {
+            const uint32_t v0 = a[m][c], v1 = a[m][c + 1], v2 = a[m][c + 2];
+            k0[m] = redc4((uint64_t)n00 * v0 + (uint64_t)n10 * v1 + (uint64_t)n20 * v2, p, pinv);
+            k1[m] = redc4((uint64_t)n01 * v0 + (uint64_t)n11 * v1 + (uint64_t)n21 * v2, p, pinv);
+            k2[m] = redc4((uint64_t)n02 * v0 + (uint64_t)n12 * v1 + (uint64_t)n22 * v2, p, pinv);
+          }
+        }
+#pragma unroll
+        for (int i = c + 3; i < NN; ++i) {
+          const uint32_t b0 = bcast(a[m0][i], o0), b1 = bcast(a[m1][i], o1), b2 = bcast(a[m2][i], o2);
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            if (T * m + T - 1 - S > c + 2)
+              a[m][i] = redc4((uint64_t)d3 * a[m][i] + (uint64_t)k0[m] * b0 + (uint64_t)k1[m] * b1 +
+                                  (uint64_t)k2[m] * b2, p, pinv);
+          }
+        }
+        Fast3Step<NN, T, c + 3>::run(a, p, pinv, Q, den, zero);
+      }
+    }
+  }
+};
+
 // The pivoting elimination of one matrix read again from `base` (entry
 // (i, j) at base[off[i NN + j]]).  Kept out of line so that the rare redo
 // does not add to the register pressure of the fast pass.
@@ -293,23 +364,47 @@ struct TeamFor {
   static constexpr int minb = kMinBlocks[NN];  // CTAs per SM the kernel is built for
 };
 
+// Dynamic shared memory that leaves room for at most `ctas` CTAs of the
+// condensation kernel per SM (0: none reserved, residency set by registers).
+// The kernel does not use it: it only keeps registers free for CTAs of other
+// kernels running beside it (the batched form's first-variable passes).
+static inline size_t condense_reserve_bytes(int ctas) {
+  if (ctas <= 0) return 0;
+  int dev = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+    return 0;
+  return (size_t)per_sm / (size_t)(ctas + 1) + 1024;
+}
+
 template <int NN, int HI>
 static int condense_dispatch(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay,
                              int64_t G, int64_t det_stride, int prime_lo, int nprimes,
-                             uint32_t *detvals, cudaStream_t st) {
+                             uint32_t *detvals, int ctas_per_sm, cudaStream_t st) {
   if (pl->n == NN) {
     constexpr int T = TeamFor<NN>::value;
+    auto kern = condense_kernel<NN, T, TeamFor<NN>::minb>;
+    const size_t reserve = condense_reserve_bytes(ctas_per_sm);
+    if (reserve) {
+      static PdPerDevice attr;
+      const int rc = pd_once_per_device(attr, [&] {
+        PD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        return POLYDET_OK;
+      });
+      if (rc) return rc;
+    }
     const int threads = 128;
     const int64_t teams_per_cta = threads / T;
     EntryOff<NN> off;
     for (int e = 0; e < NN * NN; ++e) off.o[e] = (int64_t)pl->ent[e] * lay.entry;
     dim3 grid((unsigned)((G + teams_per_cta - 1) / teams_per_cta), (unsigned)nprimes);
-    condense_kernel<NN, T, TeamFor<NN>::minb><<<grid, threads, 0, st>>>(
-        evals, detvals, G, det_stride, lay, (int64_t)pl->nent * lay.entry, pl->d_mod, pl->d_rn, prime_lo, off);
+    kern<<<grid, threads, reserve, st>>>(evals, detvals, G, det_stride, lay, (int64_t)pl->nent * lay.entry,
+                                         pl->d_mod, pl->d_rn, prime_lo, off);
     PD_CUDA(cudaGetLastError());
     return POLYDET_OK;
   }
   if constexpr (NN < HI)
-    return condense_dispatch<NN + 1, HI>(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
+    return condense_dispatch<NN + 1, HI>(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals,
+                                         ctas_per_sm, st);
   return POLYDET_EINVAL;
 }

@@ -3,21 +3,21 @@
 #include "common.cuh"
 
 int pd_condense_from_1(const polydet_plan_s *, const uint32_t *, EvLayout, int64_t, int64_t, int, int,
-                         uint32_t *, cudaStream_t);
+                         uint32_t *, int, cudaStream_t);
 int pd_condense_from_7(const polydet_plan_s *, const uint32_t *, EvLayout, int64_t, int64_t, int, int,
-                         uint32_t *, cudaStream_t);
+                         uint32_t *, int, cudaStream_t);
 int pd_condense_from_11(const polydet_plan_s *, const uint32_t *, EvLayout, int64_t, int64_t, int, int,
-                         uint32_t *, cudaStream_t);
+                         uint32_t *, int, cudaStream_t);
 int pd_condense_from_13(const polydet_plan_s *, const uint32_t *, EvLayout, int64_t, int64_t, int, int,
-                         uint32_t *, cudaStream_t);
+                         uint32_t *, int, cudaStream_t);
 int pd_condense_from_17(const polydet_plan_s *, const uint32_t *, EvLayout, int64_t, int64_t, int, int,
-                         uint32_t *, cudaStream_t);
+                         uint32_t *, int, cudaStream_t);
 int pd_condense_from_21(const polydet_plan_s *, const uint32_t *, EvLayout, int64_t, int64_t, int, int,
-                         uint32_t *, cudaStream_t);
+                         uint32_t *, int, cudaStream_t);
 int pd_condense_from_25(const polydet_plan_s *, const uint32_t *, EvLayout, int64_t, int64_t, int, int,
-                         uint32_t *, cudaStream_t);
+                         uint32_t *, int, cudaStream_t);
 int pd_condense_from_29(const polydet_plan_s *, const uint32_t *, EvLayout, int64_t, int64_t, int, int,
-                         uint32_t *, cudaStream_t);
+                         uint32_t *, int, cudaStream_t);
 int pd_fused_from_1(int, const FusedSeg *, int, int64_t, const uint32_t *, uint32_t *,
                    unsigned long long *, int, int, size_t, int, cudaStream_t);
 int pd_fused_occ_from_1(int, int, size_t, int, int *);
@@ -44,23 +44,23 @@ int pd_fused_from_29(int, const FusedSeg *, int, int64_t, const uint32_t *, uint
 int pd_fused_occ_from_29(int, int, size_t, int, int *);
 
 int pd_launch_condense(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay, int prime_lo,
-                       int nprimes, uint32_t *detvals, cudaStream_t st) {
-  return pd_launch_condense_nodes(pl, evals, lay, pl->G, pl->G, prime_lo, nprimes, detvals, st);
+                       int nprimes, uint32_t *detvals, cudaStream_t st, int ctas_per_sm) {
+  return pd_launch_condense_nodes(pl, evals, lay, pl->G, pl->G, prime_lo, nprimes, detvals, st, ctas_per_sm);
 }
 
 int pd_launch_condense_nodes(const polydet_plan_s *pl, const uint32_t *evals, EvLayout lay, int64_t G,
                              int64_t det_stride, int prime_lo, int nprimes, uint32_t *detvals,
-                             cudaStream_t st) {
+                             cudaStream_t st, int ctas_per_sm) {
   const int n = pl->n;
   if (n < 1 || G < 1) return POLYDET_EINVAL;
-  if (n <= 6) return pd_condense_from_1(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
-  if (n <= 10) return pd_condense_from_7(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
-  if (n <= 12) return pd_condense_from_11(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
-  if (n <= 16) return pd_condense_from_13(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
-  if (n <= 20) return pd_condense_from_17(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
-  if (n <= 24) return pd_condense_from_21(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
-  if (n <= 28) return pd_condense_from_25(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
-  if (n <= 32) return pd_condense_from_29(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, st);
+  if (n <= 6) return pd_condense_from_1(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, ctas_per_sm, st);
+  if (n <= 10) return pd_condense_from_7(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, ctas_per_sm, st);
+  if (n <= 12) return pd_condense_from_11(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, ctas_per_sm, st);
+  if (n <= 16) return pd_condense_from_13(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, ctas_per_sm, st);
+  if (n <= 20) return pd_condense_from_17(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, ctas_per_sm, st);
+  if (n <= 24) return pd_condense_from_21(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, ctas_per_sm, st);
+  if (n <= 28) return pd_condense_from_25(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, ctas_per_sm, st);
+  if (n <= 32) return pd_condense_from_29(pl, evals, lay, G, det_stride, prime_lo, nprimes, detvals, ctas_per_sm, st);
   return POLYDET_EINVAL;
 }
 

@@ -59,6 +59,18 @@ PD_D uint32_t redc3(uint64_t x, uint32_t p, uint32_t pinv) {  // x < 3 p^2, p <=
   return min(r, r - p);
 }
 
+// x / R mod p for x < 4 p^2 (a sum of up to four products of residues) and
+// any p < 2^31: with hi = floor(x / 2^32) < 4 p^2 / 2^32 < 2p and
+// mh = umulhi(m, p) < p, the REDC value hi - mh lies in (-p, 2p); its sign is
+// hi < mh, after which one conditional subtraction reaches [0, p).
+PD_D uint32_t redc4(uint64_t x, uint32_t p, uint32_t pinv) {
+  const uint32_t m = (uint32_t)x * pinv;
+  const uint32_t hi = (uint32_t)(x >> 32), mh = __umulhi(m, p);
+  uint32_t r = hi - mh;
+  r = (hi < mh) ? r + p : r;
+  return min(r, r - p);
+}
+
 PD_D uint32_t mfms3(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e, uint32_t f,
                     uint32_t p, uint32_t pinv) {
   return redc3((uint64_t)a * b + (uint64_t)c * d + (uint64_t)e * f, p, pinv);
