@@ -657,7 +657,7 @@ def structured_leg(st, hbm_peak, derived_upd):
 def run_ours(args, world, rank, local):
     import torch
     from paper_2010_12117_gb300 import synth
-    from paper_2010_12117_gb300.binding import probe_int_peaks
+    from paper_2010_12117_gb300.binding import condense_steps, probe_int_peaks
     from paper_2010_12117_gb300.runner import BatchedRunner, PlainRunner, StageTimer
 
     torch.cuda.set_device(local)
@@ -757,19 +757,53 @@ def run_ours(args, world, rank, local):
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    imad_s, upd1_s, pair_s = probe_int_peaks(st)
-    upd_s = 2.0 * pair_s  # each two-step element update stands for two updates
+    imad_s, upd1_s, pair_s, triple_s = probe_int_peaks(st)
     sms = dev_props.multi_processor_count
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # 64 IMAD lanes per SM per clock; the condensation kernel takes its
-    # elimination steps in pairs, and one element update of a pair - which
-    # stands for two algorithmic updates - issues three 32x32->64-bit
-    # multiply-adds (two IMAD-pipe slots each), one IMAD and one IMAD.HI:
-    # 8 slots per 2 updates
-    derived_upd = sms * 64 * sm_mhz * 1e6 / 4.0
-    peak_src = (f"derived: {sms} SMs x 64 IMAD/clk x {sm_mhz:.0f} MHz / 4 slots per update "
-                "(8 per element update of a step pair)")
-    single_step_upd = sms * 64 * sm_mhz * 1e6 / 6.0
+    lanes = sms * 64 * sm_mhz * 1e6  # IMAD lanes per second (64 per SM per clock)
+    # The condensation kernel of order n takes its elimination steps two or
+    # three at a time (condense_steps).  One element update of a step pair
+    # (two algorithmic updates) issues three 32x32->64-bit multiply-adds (two
+    # IMAD-pipe slots each), one IMAD and one IMAD.HI: 8 slots, 4 per update;
+    # one of a step triple (three updates) four multiply-adds and the same
+    # two: 10 slots, 10/3 per update.  The probes measure both element
+    # updates in registers.
+    slots = {2: 4.0, 3: 10.0 / 3.0}
+    probe_upd = {2: 2.0 * pair_s, 3: 3.0 * triple_s}
+    step_of = {n_: condense_steps(n_) for n_ in range(1, 33)}
+
+    def model_peak(n_):
+        return lanes / slots[step_of[n_]]
+    single_step_upd = lanes / 6.0
+    peak_src = (f"derived: {sms} SMs x 64 IMAD/clk x {sm_mhz:.0f} MHz / IMAD slots per update "
+                "of each order's pass (4 for a step pair, 10/3 for a step triple), weighted by "
+                "each order's updates")
+    # per order: the update rate against its integer-pipe peak, the byte rate
+    # against HBM, and the time either bound alone allows; the sum of those
+    # times over the sum of the measured ones is the kernel's fraction of its
+    # launch-by-launch roofline (small orders read 4 n^2 bytes for only
+    # (n-1) n (2n-1) / 6 updates and are HBM-bound)
+    by_order, t_bound, t_meas = {}, 0.0, 0.0
+    t_model = t_probe = upd_all = 0.0
+    for n_, (ms_, upd) in sorted(ptimer.tag_ms("condense").items()):
+        byt = bytes_by_order[n_]
+        pk = model_peak(n_)
+        tb = max(upd / pk, byt / (hbm_peak * 1e9))
+        t_bound += tb
+        t_meas += ms_ * 1e-3
+        t_model += upd / pk
+        t_probe += upd / probe_upd[step_of[n_]]
+        upd_all += upd
+        by_order[str(n_)] = {"ms": ms_, "steps_per_pass": step_of[n_], "Gupdate_s": upd / (ms_ * 1e-3) / 1e9,
+                             "alu_frac": upd / (ms_ * 1e-3) / pk,
+                             "alu_frac_of_probe": upd / (ms_ * 1e-3) / probe_upd[step_of[n_]],
+                             "alu_frac_of_single_step_peak": upd / (ms_ * 1e-3) / single_step_upd,
+                             "hbm_frac": byt / (ms_ * 1e-3) / (hbm_peak * 1e9),
+                             "bound": "alu" if upd / pk >= byt / (hbm_peak * 1e9) else "hbm"}
+    # the batch's work-weighted ceilings (the batched form condenses the same
+    # determinants of every order)
+    derived_upd = upd_all / t_model if t_model else lanes / 4.0
+    upd_s = upd_all / t_probe if t_probe else 2.0 * pair_s
 
     def roofs_of(stage_ms, work):
         roofs = {}
@@ -790,22 +824,6 @@ def run_ours(args, world, rank, local):
     plain_roofs = roofs_of(plain_stage_ms, dict(ptimer.work))
     # the dominant kernel: the condensation kernel, timed launch by launch
     nl = ptimer.launches["condense"]
-    # per order: the update rate against the integer-pipe peak, the byte rate
-    # against HBM, and the time either bound alone allows; the sum of those
-    # times over the sum of the measured ones is the kernel's fraction of its
-    # launch-by-launch roofline (small orders read 4 n^2 bytes for only
-    # (n-1) n (2n-1) / 6 updates and are HBM-bound)
-    by_order, t_bound, t_meas = {}, 0.0, 0.0
-    for n_, (ms_, upd) in sorted(ptimer.tag_ms("condense").items()):
-        byt = bytes_by_order[n_]
-        tb = max(upd / derived_upd, byt / (hbm_peak * 1e9))
-        t_bound += tb
-        t_meas += ms_ * 1e-3
-        by_order[str(n_)] = {"ms": ms_, "Gupdate_s": upd / (ms_ * 1e-3) / 1e9,
-                             "alu_frac": upd / (ms_ * 1e-3) / derived_upd,
-                             "alu_frac_of_single_step_peak": upd / (ms_ * 1e-3) / single_step_upd,
-                             "hbm_frac": byt / (ms_ * 1e-3) / (hbm_peak * 1e9),
-                             "bound": "alu" if upd / derived_upd >= byt / (hbm_peak * 1e9) else "hbm"}
     ratio = _traffic_ratio()
     roof = dict(plain_roofs["condense"], kernel="condense_kernel", launches=nl,
                 avg_launch_ms=plain_stage_ms["condense"] / max(1, nl),
@@ -815,6 +833,7 @@ def run_ours(args, world, rank, local):
                 traffic_src=("ncu read + write / algorithmic bytes of the n = 24 capture, scaled to "
                              "the average launch" if ratio is not None else
                              "sources changed since the ncu capture"),
+                imad_pipe_active_ncu=CONDENSE_TRAFFIC.get("fmaheavy_active") if ratio is not None else None,
                 by_order=by_order,
                 frac_of_launch_bound=t_bound / t_meas if t_meas else None,
                 timed="CUDA events around each of its launches on the launching stream, plain "
@@ -823,7 +842,7 @@ def run_ours(args, world, rank, local):
 
     served = None if args.no_served else served_leg(args, mats, value, st)
     kernels = None if args.no_kernels else kernel_leg(st, hbm_peak, mats)
-    structured = None if args.no_structured else structured_leg(st, hbm_peak, derived_upd)
+    structured = None if args.no_structured else structured_leg(st, hbm_peak, model_peak(15))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -865,7 +884,8 @@ def run_ours(args, world, rank, local):
         "stage_ms": stage_ms,
         "stage_events": "CUDA events between the per-stage graph launches of every timed step",
         "int_probe": {"imad_per_s": imad_s, "single_step_update_per_s": upd1_s,
-                      "pair_element_update_per_s": pair_s, "update_per_s_two_step": upd_s},
+                      "pair_element_update_per_s": pair_s, "triple_element_update_per_s": triple_s,
+                      "update_per_s_weighted": upd_s},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "exact dets/s", "pipelined": True, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

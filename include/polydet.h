@@ -417,6 +417,10 @@ int polydet_batch_test_drop_copies(polydet_batch_t batch, int on);
  * (a CTA size must be a multiple of it); POLYDET_EINVAL outside 1..32.  Host
  * only: no device call. */
 int polydet_team_size(int n);
+/* Elimination steps the condensation kernels of order n take per pass (2 or
+ * 3; the instruction mix, and so the integer-pipe ceiling, depends on it);
+ * POLYDET_EINVAL outside 1..32.  Host only. */
+int polydet_condense_steps(int n);
 
 /* Stage 1 of a batch (Sec. 3.1): every variable but the last (fused orders)
  * or but the first (materialized orders); all orders (n = 0 in
@@ -470,15 +474,16 @@ int polydet_mlp_backward(const float *params, const float *x, const float *targe
 int polydet_mlp_adam(float *params, const float *grads, float *m, float *v, int step, float lr,
                      float beta1, float beta2, float eps, float weight_decay, void *stream);
 
-/* Measurement utility (not a stage of the method): runs three in-register
+/* Measurement utility (not a stage of the method): runs four in-register
  * integer streams on every SM and reports their rates, the ceilings of the
  * condensation kernels - plain 32-bit multiply-adds per second, single-step
- * modular updates (a*b - c*d)/2^32 mod p per second, and the two-step
- * element updates (a*b + c*d + e*f)/2^32 mod p per second (each stands for
- * two single-step updates).  Allocates and frees a small buffer;
- * synchronises `stream`. */
+ * modular updates (a*b - c*d)/2^32 mod p per second, two-step element
+ * updates (a*b + c*d + e*f)/2^32 mod p per second (each stands for two
+ * single-step updates) and three-step element updates
+ * (a*b + c*d + e*f + g*h)/2^32 mod p per second (each stands for three).
+ * Allocates and frees a small buffer; synchronises `stream`. */
 int polydet_probe_int_peaks(void *stream, double *imad_per_s, double *update_per_s,
-                            double *pair_update_per_s);
+                            double *pair_update_per_s, double *triple_update_per_s);
 
 /* Last CUDA error string seen by the library (host, static storage). */
 const char *polydet_last_error(void);

@@ -121,7 +121,9 @@ SIGNATURES = {
     "polydet_mlp_adam": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.c_float, ctypes.c_float,
                               ctypes.c_float, ctypes.c_float, ctypes.c_float, _VP]),
     "polydet_probe_int_peaks": (_I, [_VP, ctypes.POINTER(ctypes.c_double),
-                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "polydet_condense_steps": (_I, [_I]),
     "polydet_last_error": (ctypes.c_char_p, []),
 }
 
@@ -559,16 +561,25 @@ def mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, we
                                   float(weight_decay), _stream(stream)), "polydet_mlp_adam")
 
 
-def probe_int_peaks(stream=None) -> tuple[float, float, float]:
+def probe_int_peaks(stream=None) -> tuple[float, float, float, float]:
     """(32-bit multiply-adds per second, single-step modular updates per
-    second, two-step element updates per second) measured on the current
-    device by the library's probe kernels."""
+    second, two-step element updates per second, three-step element updates
+    per second) measured on the current device by the library's probes."""
     a = ctypes.c_double(0)
     u = ctypes.c_double(0)
+    u2 = ctypes.c_double(0)
     u3 = ctypes.c_double(0)
-    _check(lib().polydet_probe_int_peaks(_stream(stream), ctypes.byref(a), ctypes.byref(u), ctypes.byref(u3)),
-           "polydet_probe_int_peaks")
-    return a.value, u.value, u3.value
+    _check(lib().polydet_probe_int_peaks(_stream(stream), ctypes.byref(a), ctypes.byref(u), ctypes.byref(u2),
+                                         ctypes.byref(u3)), "polydet_probe_int_peaks")
+    return a.value, u.value, u2.value, u3.value
+
+
+def condense_steps(n: int) -> int:
+    """Elimination steps per pass of the condensation kernels of order n."""
+    t = lib().polydet_condense_steps(int(n))
+    if t < 1:
+        _check(t, "polydet_condense_steps")
+    return t
 
 
 def limbs_to_ints(limbs: np.ndarray, W: int) -> List[int]:

@@ -20,10 +20,12 @@
 // as prod_{c<n-1} Q_c with Q_c = prod_{j<=c} v_jj, and inverted once by
 // Fermat's little theorem at the end, instead of one inverse per step.
 //
-// The fast pass takes the steps two at a time (Fast2Step: the Schur
-// complement of the leading 2 x 2 block, one three-product sum and one REDC
-// per element and pair of steps) and runs without any search and without a
-// warp vote per step; a zero pivot (a zero 2 x 2 minor) is only recorded.
+// The fast pass takes the steps two or three at a time, per order (Fast2Step:
+// the Schur complement of the leading 2 x 2 block, one three-product sum and
+// one REDC per element and pair of steps; Fast3Step: of the leading 3 x 3
+// block, four products and one REDC per element and triple of steps) and runs
+// without any search and without a warp vote per step; a zero pivot (a zero
+// block determinant) is only recorded.
 // Pivot search (Algorithm 3's first nonzero entry), for the rare warp that
 // met one: the matrices are redone one step at a time (ElimStep, out of
 // line); when the pivot a_cc is zero, the first row r > c with a_rc != 0 is
@@ -328,12 +330,17 @@ __global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__r
 
   uint32_t Q = md.r1, den = md.r1;
   bool zero = false;
-  Fast2Step<NN, T, 0>::run(a, p, pinv, Q, den, zero);
-  // primes above PD_FOLD3_MAX (only plans of more than 67 primes reach them)
-  // redo every matrix with the pivoting elimination (the fast pass is not
-  // skipped: a branch around it costs the common case its register
-  // allocation)
-  zero |= p > PD_FOLD3_MAX;
+  constexpr int STEP = kStep[NN];
+  if constexpr (STEP == 3) {
+    Fast3Step<NN, T, 0>::run(a, p, pinv, Q, den, zero);
+  } else {
+    Fast2Step<NN, T, 0>::run(a, p, pinv, Q, den, zero);
+    // the two-step pass needs p <= PD_FOLD3_MAX: larger primes (only plans of
+    // more than 67 primes reach them) redo every matrix with the pivoting
+    // elimination (the fast pass is not skipped: a branch around it costs
+    // the common case its register allocation)
+    zero |= p > PD_FOLD3_MAX;
+  }
   if (__any_sync(PD_FULL, zero)) {  // some matrix of this warp met a zero pivot
     const uint2 qd = elim_search<NN, T>(base, off.o, t, md);
     Q = qd.x;
@@ -362,6 +369,7 @@ template <int NN>
 struct TeamFor {
   static constexpr int value = kTeam[NN];      // lanes per matrix
   static constexpr int minb = kMinBlocks[NN];  // CTAs per SM the kernel is built for
+  static constexpr int step = kStep[NN];       // steps per pass of the fast elimination
 };
 
 // Dynamic shared memory that leaves room for at most `ctas` CTAs of the

@@ -97,3 +97,7 @@ int pd_fused_team(int n) { return (n >= 1 && n <= POLYDET_MAX_N) ? kTeam[n] : 1;
 extern "C" int polydet_team_size(int n) {
   return (n >= 1 && n <= POLYDET_MAX_N) ? kTeam[n] : POLYDET_EINVAL;
 }
+
+extern "C" int polydet_condense_steps(int n) {
+  return (n >= 1 && n <= POLYDET_MAX_N) ? kStep[n] : POLYDET_EINVAL;
+}

@@ -127,8 +127,12 @@ __device__ __noinline__ uint2 fused_det(const uint32_t *mine, int bd, int t, Mod
   }
   uint32_t Q = md.r1, den = md.r1;
   bool zero = false;
-  Fast2Step<NN, T, 0>::run(a, p, pinv, Q, den, zero);
-  zero |= p > PD_FOLD3_MAX;  // as in condense_kernel: larger primes redo every matrix
+  if constexpr (kStep[NN] == 3) {
+    Fast3Step<NN, T, 0>::run(a, p, pinv, Q, den, zero);
+  } else {
+    Fast2Step<NN, T, 0>::run(a, p, pinv, Q, den, zero);
+    zero |= p > PD_FOLD3_MAX;  // as in condense_kernel: larger primes redo every matrix
+  }
   if (__any_sync(PD_FULL, zero))  // a zero pivot in this warp: redo with the search
     return fused_det_search<NN, T>(mine, bd, t, md);
   return make_uint2(Q, den);

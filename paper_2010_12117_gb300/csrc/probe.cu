@@ -1,13 +1,14 @@
 // Measurement utility: the integer-pipe ceilings that bound condensation.
 //
-// Three in-register streams with eight independent dependency chains per
+// Four in-register streams with eight independent dependency chains per
 // thread, enough warps per SM to hide latency, and no memory traffic:
 //  - plain 32-bit multiply-adds (x = x * x + c), the IMAD rate;
 //  - the single-step update r = (a*b - c*d) / R mod p (two 32x32->64
 //    multiply-adds, one REDC), the fused-update rate;
 //  - the two-step element update r = (a*b + c*d + e*f) / R mod p (three
-//    multiply-adds, one REDC; each stands for two single-step updates), the
-//    rate that bounds the condensation kernels' fast pass.
+//    multiply-adds, one REDC; each stands for two single-step updates) and
+//    the three-step one (four multiply-adds, one REDC; three updates), the
+//    rates that bound the condensation kernels' fast pass.
 // The rates bound the determinant kernels the way a copy bounds a memory
 // kernel.
 #include "common.cuh"
@@ -69,9 +70,34 @@ __global__ void __launch_bounds__(256) pair_probe(uint32_t *out, int iters, uint
   if (s == 0x12345678u) out[tid] = s;
 }
 
+__global__ void __launch_bounds__(256) triple_probe(uint32_t *out, int iters, uint32_t p,
+                                                    uint32_t pinv, uint32_t seed) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t a[8], b[8], e[8], g[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    a[j] = (seed + tid * 8u + j) % p;
+    b[j] = (seed * 3u + j * 7919u) % p;
+    e[j] = (seed * 5u + j * 104729u) % p;
+    g[j] = (seed * 7u + j * 1299709u) % p;
+  }
+  const uint32_t d3 = (seed ^ 0x5bd1e995u) % p, c0 = (seed + 12345u) % p, c1 = (seed + 54321u) % p,
+                 c2 = (seed + 99991u) % p;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      a[j] = redc4((uint64_t)d3 * a[j] + (uint64_t)c0 * b[j] + (uint64_t)c1 * e[j] + (uint64_t)c2 * g[j], p,
+                   pinv);
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s ^= a[j];
+  if (s == 0x12345678u) out[tid] = s;
+}
+
 extern "C" int polydet_probe_int_peaks(void *stream, double *imad_per_s, double *update_per_s,
-                                       double *pair_update_per_s) {
-  if (!imad_per_s || !update_per_s || !pair_update_per_s) return POLYDET_EINVAL;
+                                       double *pair_update_per_s, double *triple_update_per_s) {
+  if (!imad_per_s || !update_per_s || !pair_update_per_s || !triple_update_per_s) return POLYDET_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0, sms = 0;
   PD_CUDA(cudaGetDevice(&dev));
@@ -112,6 +138,13 @@ extern "C" int polydet_probe_int_peaks(void *stream, double *imad_per_s, double 
   PD_CUDA(cudaEventSynchronize(e1));
   PD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   *pair_update_per_s = (double)blocks * threads * (iters / 4) * 8.0 / (ms * 1e-3);
+  triple_probe<<<blocks, threads, 0, st>>>(out, iters / 4, p, pinv, 1u);
+  PD_CUDA(cudaEventRecord(e0, st));
+  triple_probe<<<blocks, threads, 0, st>>>(out, iters / 4, p, pinv, 2u);
+  PD_CUDA(cudaEventRecord(e1, st));
+  PD_CUDA(cudaEventSynchronize(e1));
+  PD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  *triple_update_per_s = (double)blocks * threads * (iters / 4) * 8.0 / (ms * 1e-3);
   PD_CUDA(cudaFreeAsync(out, st));
   PD_CUDA(cudaStreamSynchronize(st));
   cudaEventDestroy(e0);

@@ -280,3 +280,24 @@ def test_fused_staging_with_one_buffer_and_unaligned_rows():
     got = batched_results(mats, modes=BATCH_FUSED)
     for pm, g in zip(mats, got):
         assert g == plain(pm), (pm.n, pm.degs)
+
+
+@pytest.mark.parametrize("ctas", [1, 2])
+def test_condensation_residency_cap_gives_the_same_results(ctas):
+    """Capping the materialized orders' condensation CTAs per SM (reserved
+    shared memory) changes only where the kernels run, not the integers."""
+    from paper_2010_12117_gb300.binding import BATCH_MATERIALIZED
+    from paper_2010_12117_gb300.runner import BatchedRunner
+    mats = _mixed()[10:20]
+    want = batched_results(mats, modes=BATCH_MATERIALIZED)
+    st = torch.cuda.Stream()
+    r = BatchedRunner(mats, tune=False, stream=st)
+    r.set_modes(BATCH_MATERIALIZED)
+    r.batch.set_condense_ctas(ctas)
+    r.upload(st)
+    r.compute(st)
+    r.download(st)
+    st.synchronize()
+    r.check_status(st)
+    assert r.results() == want
+    r.close()
