@@ -33,12 +33,14 @@ sys.path.insert(0, ROOT)
 METRIC = ("exact poly determinants/sec and mod-p n×n dets/sec; IMAD % and HBM GB/s of peak")
 # DRAM traffic of condense_kernel measured by ncu (read + write over the
 # algorithmic bytes 4 n^2 + 4 per determinant, from one capture of a single
-# 24 x 24 launch), valid only for the code it was taken on: digests of the
+# 24 x 24 launch, with the IMAD pipe's active fraction from the same
+# capture), valid only for the code it was taken on: digests of the
 # kernel's sources with comments and blank space removed; the bench reports
 # traffic null once they change.
-CONDENSE_TRAFFIC = {"ratio": 1.0166, "sources": {"paper_2010_12117_gb300/csrc/condense.cuh": "47d5180bc86c0325",
-                                                "paper_2010_12117_gb300/csrc/modarith.cuh": "263c5135aa162b64",
-                                                "paper_2010_12117_gb300/csrc/teams.cuh": "e9621d4034187305"}}
+CONDENSE_TRAFFIC = {"ratio": 1.0162, "fmaheavy_active": 0.709,
+                    "sources": {"paper_2010_12117_gb300/csrc/condense.cuh": "45152f83d787e029",
+                                "paper_2010_12117_gb300/csrc/modarith.cuh": "b36f048e62c9ded4",
+                                "paper_2010_12117_gb300/csrc/teams.cuh": "8bc43e619bd6d39c"}}
 
 
 def _code_digest(path: str) -> str:
