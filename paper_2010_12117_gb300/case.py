@@ -7,7 +7,8 @@ runs condense_kernel<24, ...> on 73 x 73 nodes per prime (plain form, then
 the batched form in the chosen mode) and prints the job's sizes.  Other
 stages: ``--stage eval`` / ``--stage crt`` run one stage alone on inputs
 larger than L2, and ``--stage batched`` runs one profiled step of the
-256-matrix batched workload (between cudaProfilerStart and Stop).
+256-matrix batched workload (between cudaProfilerStart and Stop);
+``--stage probe`` runs the integer-pipe probes of polydet_probe_int_peaks.
 """
 from __future__ import annotations
 
@@ -25,12 +26,12 @@ def main(argv=None) -> int:
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--mode", choices=("default", "fused", "materialized"), default="default")
     ap.add_argument("--chunk-words", type=int, default=0, help="materialized chunk budget (0: default)")
-    ap.add_argument("--stage", choices=("det", "eval", "crt", "batched"), default="det",
+    ap.add_argument("--stage", choices=("det", "eval", "crt", "batched", "probe"), default="det",
                     help="det: the whole job in both forms; eval: the evaluation of the 12x12 "
                          "trivariate workload alone; crt: the CRT of 2^24 coefficients alone; "
                          "batched: two steps of the 256-matrix batched workload (seed 0, the "
                          "autotuner's cached choices, CUDA graphs), the second between "
-                         "cudaProfilerStart and cudaProfilerStop")
+                         "cudaProfilerStart and cudaProfilerStop; probe: the integer-pipe probes")
     ap.add_argument("--primes", type=int, default=5, help="primes for --stage eval / crt")
     ap.add_argument("--full-grid", action="store_true", help="--stage eval on the power-of-two grid")
     args = ap.parse_args(argv)
@@ -38,6 +39,12 @@ def main(argv=None) -> int:
     import torch
     if args.stage == "batched":
         return _batched()
+    if args.stage == "probe":
+        from paper_2010_12117_gb300 import binding
+        imad, upd, pair, triple = binding.probe_int_peaks()
+        print(f"ok probes: {imad:.4g} IMAD/s, {upd:.4g} single-step updates/s, "
+              f"{pair:.4g} two-step element updates/s, {triple:.4g} three-step element updates/s")
+        return 0
     if args.stage != "det":
         return _stage(args)
     from . import synth
