@@ -54,11 +54,19 @@ def _code_digest(path: str) -> str:
     return hashlib.sha256(s.encode()).hexdigest()[:16]
 
 
+def _sources_match(sources: dict) -> bool:
+    return all(_code_digest(path) == h for path, h in sources.items())
+
+
 def _traffic_ratio():
-    for path, h in CONDENSE_TRAFFIC["sources"].items():
-        if _code_digest(path) != h:
-            return None
-    return CONDENSE_TRAFFIC["ratio"]
+    return CONDENSE_TRAFFIC["ratio"] if _sources_match(CONDENSE_TRAFFIC["sources"]) else None
+
+
+# Active fraction of the FMA-heavy (IMAD) pipe in crt_kernel_p<11> on 2^24
+# coefficients, from one ncu capture, valid for the sources it was taken on.
+CRT_PIPE = {"fmaheavy_active": {11: 0.843},
+            "sources": {"paper_2010_12117_gb300/csrc/crt.cu": "b7f51ef1688995fc",
+                        "paper_2010_12117_gb300/csrc/modarith.cuh": "b36f048e62c9ded4"}}
 
 
 WORKLOAD = ("batched: 256 matrices, n~U[4,24], k~U{1,2,3}, d_v~U[1,4], density~U[0.3,1.0], "
@@ -467,6 +475,10 @@ def kernel_leg(st, hbm_peak, mats):
         # the integer side: Garner P (P - 1) / 2 mulmods and P W limb products
         mulmods = float(C) * (P * (P - 1) / 2 + P * W)
         out[f"crt_2^24_P{P}"] = dict(hbm(ms, byts), W=W, mulmods_per_s=mulmods / (ms * 1e-3))
+        pipe = CRT_PIPE["fmaheavy_active"].get(P)
+        if pipe is not None and _sources_match(CRT_PIPE["sources"]):
+            # the integer multiply pipe, not memory, bounds it (ncu)
+            out[f"crt_2^24_P{P}"].update(bound="imad", imad_pipe_active_ncu=pipe)
         pc.close()
         del res, limbs
     torch.cuda.empty_cache()

@@ -119,18 +119,19 @@ static int ilog2(int64_t x) {
 
 template <int CPT>
 static int launch_direct(const TxArgs &a, int64_t ncols, int items, int nprimes, cudaStream_t st) {
-  dim3 grid((unsigned)((ncols + 256 * CPT - 1) / (256 * CPT)), (unsigned)items, (unsigned)nprimes);
+  constexpr int TH = kDirectThreads;
+  dim3 grid((unsigned)((ncols + TH * CPT - 1) / (TH * CPT)), (unsigned)items, (unsigned)nprimes);
   if (a.flat_items)
-    grid = dim3((unsigned)((ncols * items * a.flat_groups + 255) / 256), 1u, (unsigned)nprimes);
+    grid = dim3((unsigned)((ncols * items * a.flat_groups + TH - 1) / TH), 1u, (unsigned)nprimes);
   switch (a.Lin) {
-    case 1: coltx_direct_kernel<1, CPT><<<grid, 256, 0, st>>>(a); break;
-    case 2: coltx_direct_kernel<2, CPT><<<grid, 256, 0, st>>>(a); break;
-    case 3: coltx_direct_kernel<3, CPT><<<grid, 256, 0, st>>>(a); break;
-    case 4: coltx_direct_kernel<4, CPT><<<grid, 256, 0, st>>>(a); break;
-    case 5: coltx_direct_kernel<5, CPT><<<grid, 256, 0, st>>>(a); break;
-    case 6: coltx_direct_kernel<6, CPT><<<grid, 256, 0, st>>>(a); break;
-    case 7: coltx_direct_kernel<7, CPT><<<grid, 256, 0, st>>>(a); break;
-    default: coltx_direct_kernel<8, CPT><<<grid, 256, 0, st>>>(a); break;
+    case 1: coltx_direct_kernel<1, CPT><<<grid, TH, 0, st>>>(a); break;
+    case 2: coltx_direct_kernel<2, CPT><<<grid, TH, 0, st>>>(a); break;
+    case 3: coltx_direct_kernel<3, CPT><<<grid, TH, 0, st>>>(a); break;
+    case 4: coltx_direct_kernel<4, CPT><<<grid, TH, 0, st>>>(a); break;
+    case 5: coltx_direct_kernel<5, CPT><<<grid, TH, 0, st>>>(a); break;
+    case 6: coltx_direct_kernel<6, CPT><<<grid, TH, 0, st>>>(a); break;
+    case 7: coltx_direct_kernel<7, CPT><<<grid, TH, 0, st>>>(a); break;
+    default: coltx_direct_kernel<8, CPT><<<grid, TH, 0, st>>>(a); break;
   }
   PD_CUDA(cudaGetLastError());
   return POLYDET_OK;
@@ -146,8 +147,11 @@ static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
   const bool window_ok = a.row_hi == 0 || (a.olp > 1 && a.olp == lp_in && a.row_lo % lp_in == 0);
   if (!a.inverse && a.Lin <= 8 && rows_ok && window_ok && (a.olp <= 1 || a.olp == lp_in)) {
     // columns per thread: more share each coset's twiddles, fewer leave
-    // fewer idle lanes in the last CTA of a row of B columns
-    const int cpt = a.B < 8 ? 1 : (ncols >= 8192 ? 4 : (ncols >= 2048 ? 2 : 1));
+    // fewer idle lanes in the last CTA of a row of B columns (measured: two
+    // per thread from rows of about 1000 columns on; four only for inputs of
+    // at most five words, whose registers still allow two CTAs per SM)
+    int cpt = a.B < 8 ? 1 : (ncols >= 8192 ? 4 : (ncols >= 1024 ? 2 : 1));
+    if (cpt == 4 && a.Lin > 5) cpt = 2;
     // short rows (one column per thread): one grid axis over (item, column)
     // pairs, so that rows shorter than a CTA, or a row's last CTA, leave no
     // threads idle

@@ -1,7 +1,11 @@
 // Measurement utility: the integer-pipe ceilings that bound condensation.
 //
-// Four in-register streams with eight independent dependency chains per
-// thread, enough warps per SM to hide latency, and no memory traffic:
+// Four in-register streams with eight independent values per thread, enough
+// warps per SM to hide latency, and no memory traffic.  Every product of an
+// iteration takes at least one operand computed in the previous iteration
+// (value j is updated from values j, j + 1, ... of the last round), so that
+// no product is loop-invariant and none can be hoisted out of the loop, as
+// in the elimination, where every operand is a run-time value:
 //  - plain 32-bit multiply-adds (x = x * x + c), the IMAD rate;
 //  - the single-step update r = (a*b - c*d) / R mod p (two 32x32->64
 //    multiply-adds, one REDC), the fused-update rate;
@@ -32,16 +36,16 @@ __global__ void __launch_bounds__(256) imad_probe(uint32_t *out, int iters, uint
 __global__ void __launch_bounds__(256) update_probe(uint32_t *out, int iters, uint32_t p,
                                                     uint32_t pinv, uint32_t seed) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t a[8], f[8];
+  uint32_t a[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    a[j] = (seed + tid * 8u + j) % p;
-    f[j] = (seed * 3u + j * 7919u) % p;
-  }
+  for (int j = 0; j < 8; ++j) a[j] = (seed + tid * 8u + j * 7919u) % p;
   const uint32_t piv = (seed ^ 0x5bd1e995u) % p, c = (seed + 12345u) % p;
   for (int it = 0; it < iters; ++it) {
+    uint32_t b[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = mfms(piv, a[j], f[j], c, p, pinv);
+    for (int j = 0; j < 8; ++j) b[j] = mfms(piv, a[j], a[(j + 1) & 7], c, p, pinv);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = b[j];
   }
   uint32_t s = 0;
 #pragma unroll
@@ -52,17 +56,16 @@ __global__ void __launch_bounds__(256) update_probe(uint32_t *out, int iters, ui
 __global__ void __launch_bounds__(256) pair_probe(uint32_t *out, int iters, uint32_t p,
                                                   uint32_t pinv, uint32_t seed) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t a[8], b[8], e[8];
+  uint32_t a[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    a[j] = (seed + tid * 8u + j) % p;
-    b[j] = (seed * 3u + j * 7919u) % p;
-    e[j] = (seed * 5u + j * 104729u) % p;
-  }
+  for (int j = 0; j < 8; ++j) a[j] = (seed + tid * 8u + j * 7919u) % p;
   const uint32_t d2 = (seed ^ 0x5bd1e995u) % p, c1 = (seed + 12345u) % p, c2 = (seed + 54321u) % p;
   for (int it = 0; it < iters; ++it) {
+    uint32_t b[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = mfms3(d2, a[j], c1, b[j], c2, e[j], p, pinv);
+    for (int j = 0; j < 8; ++j) b[j] = mfms3(d2, a[j], c1, a[(j + 1) & 7], c2, a[(j + 2) & 7], p, pinv);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = b[j];
   }
   uint32_t s = 0;
 #pragma unroll
@@ -73,21 +76,20 @@ __global__ void __launch_bounds__(256) pair_probe(uint32_t *out, int iters, uint
 __global__ void __launch_bounds__(256) triple_probe(uint32_t *out, int iters, uint32_t p,
                                                     uint32_t pinv, uint32_t seed) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t a[8], b[8], e[8], g[8];
+  uint32_t a[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    a[j] = (seed + tid * 8u + j) % p;
-    b[j] = (seed * 3u + j * 7919u) % p;
-    e[j] = (seed * 5u + j * 104729u) % p;
-    g[j] = (seed * 7u + j * 1299709u) % p;
-  }
+  for (int j = 0; j < 8; ++j) a[j] = (seed + tid * 8u + j * 7919u) % p;
   const uint32_t d3 = (seed ^ 0x5bd1e995u) % p, c0 = (seed + 12345u) % p, c1 = (seed + 54321u) % p,
                  c2 = (seed + 99991u) % p;
   for (int it = 0; it < iters; ++it) {
+    uint32_t b[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j)
-      a[j] = redc4((uint64_t)d3 * a[j] + (uint64_t)c0 * b[j] + (uint64_t)c1 * e[j] + (uint64_t)c2 * g[j], p,
-                   pinv);
+      b[j] = redc4((uint64_t)d3 * a[j] + (uint64_t)c0 * a[(j + 1) & 7] + (uint64_t)c1 * a[(j + 2) & 7] +
+                       (uint64_t)c2 * a[(j + 3) & 7],
+                   p, pinv);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = b[j];
   }
   uint32_t s = 0;
 #pragma unroll
