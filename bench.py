@@ -37,10 +37,10 @@ METRIC = ("exact poly determinants/sec and mod-p n×n dets/sec; IMAD % and HBM G
 # capture), valid only for the code it was taken on: digests of the
 # kernel's sources with comments and blank space removed; the bench reports
 # traffic null once they change.
-CONDENSE_TRAFFIC = {"ratio": 1.0162, "fmaheavy_active": 0.709,
-                    "sources": {"paper_2010_12117_gb300/csrc/condense.cuh": "45152f83d787e029",
+CONDENSE_TRAFFIC = {"ratio": 1.0133, "fmaheavy_active": 0.716,
+                    "sources": {"paper_2010_12117_gb300/csrc/condense.cuh": "b0dcc202ebcb755b",
                                 "paper_2010_12117_gb300/csrc/modarith.cuh": "b36f048e62c9ded4",
-                                "paper_2010_12117_gb300/csrc/teams.cuh": "8bc43e619bd6d39c"}}
+                                "paper_2010_12117_gb300/csrc/teams.cuh": "175199df75021501"}}
 
 
 def _code_digest(path: str) -> str:
@@ -779,20 +779,21 @@ def run_ours(args, world, rank, local):
     lanes = sms * 64 * sm_mhz * 1e6  # IMAD lanes per second (64 per SM per clock)
     # The condensation kernel of order n takes its elimination steps two or
     # three at a time (condense_steps).  One element update of a step pair
-    # (two algorithmic updates) issues three 32x32->64-bit multiply-adds (two
-    # IMAD-pipe slots each), one IMAD and one IMAD.HI: 8 slots, 4 per update;
-    # one of a step triple (three updates) four multiply-adds and the same
-    # two: 10 slots, 10/3 per update.  The probes measure both element
-    # updates in registers.
-    slots = {2: 4.0, 3: 10.0 / 3.0}
+    # (two algorithmic updates) issues three 32x32->64-bit multiply-adds and
+    # the REDC's IMAD and IMAD.HI; the pipe costs ncu measures on the probes
+    # (a wide multiply-add or an IMAD.HI holds the FMA-heavy pipe two slots,
+    # an IMAD one) make that 9 slots, 4.5 per update; one of a step triple
+    # (three updates) four multiply-adds and the same two: 11 slots, 11/3 per
+    # update.  The probes run both element updates in registers.
+    slots = {2: 4.5, 3: 11.0 / 3.0}
     probe_upd = {2: 2.0 * pair_s, 3: 3.0 * triple_s}
     step_of = {n_: condense_steps(n_) for n_ in range(1, 33)}
 
     def model_peak(n_):
         return lanes / slots[step_of[n_]]
-    single_step_upd = lanes / 6.0
+    single_step_upd = lanes / 6.0  # round 1's single-step model, kept for comparison
     peak_src = (f"derived: {sms} SMs x 64 IMAD/clk x {sm_mhz:.0f} MHz / IMAD slots per update "
-                "of each order's pass (4 for a step pair, 10/3 for a step triple), weighted by "
+                "of each order's pass (4.5 for a step pair, 11/3 for a step triple), weighted by "
                 "each order's updates")
     # per order: the update rate against its integer-pipe peak, the byte rate
     # against HBM, and the time either bound alone allows; the sum of those
@@ -818,7 +819,7 @@ def run_ours(args, world, rank, local):
                              "bound": "alu" if upd / pk >= byt / (hbm_peak * 1e9) else "hbm"}
     # the batch's work-weighted ceilings (the batched form condenses the same
     # determinants of every order)
-    derived_upd = upd_all / t_model if t_model else lanes / 4.0
+    derived_upd = upd_all / t_model if t_model else lanes / 4.5
     upd_s = upd_all / t_probe if t_probe else 2.0 * pair_s
 
     def roofs_of(stage_ms, work):

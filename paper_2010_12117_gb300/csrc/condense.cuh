@@ -299,8 +299,8 @@ __device__ __noinline__ uint2 elim_search(const uint32_t *base, const int64_t *o
 // G nodes per prime (node g of prime slot q: entry (i, j) at
 // evals[q prime_words + (g / rowlen) rowstride + g % rowlen + off[i n + j]]);
 // determinant of node g of prime slot q to detvals[q det_stride + g].
-template <int NN, int T, int MINB>
-__global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__restrict__ evals,
+template <int NN, int T, int MINB, int TH>
+__global__ void __launch_bounds__(TH, MINB) condense_kernel(const uint32_t *__restrict__ evals,
                                                        uint32_t *__restrict__ detvals, int64_t G,
                                                        int64_t det_stride, EvLayout lay,
                                                        int64_t prime_words,
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__r
   const ModP md = mod[q];
   const uint32_t p = md.p, pinv = md.pinv;
   const int t = (int)(threadIdx.x & (T - 1));
-  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / T;
+  const int64_t g = ((int64_t)blockIdx.x * TH + threadIdx.x) / T;
   const bool active = g < G;
   const int64_t gg = active ? g : (G - 1);
   const int64_t row = gg / lay.rowlen;
@@ -349,8 +349,8 @@ __global__ void __launch_bounds__(128, MINB) condense_kernel(const uint32_t *__r
   // Every lane of a team holds the same (Q, den): hand them to one lane per
   // determinant so that the CTA's inversions run once each, in as few warps
   // as possible, and the results are stored contiguously.
-  __shared__ uint32_t fin_q[128], fin_d[128];
-  const int S = blockDim.x / T;
+  __shared__ uint32_t fin_q[TH], fin_d[TH];
+  constexpr int S = TH / T;
   const int team = threadIdx.x / T;
   if (t == 0) {
     fin_q[team] = Q;
@@ -370,6 +370,7 @@ struct TeamFor {
   static constexpr int value = kTeam[NN];      // lanes per matrix
   static constexpr int minb = kMinBlocks[NN];  // CTAs per SM the kernel is built for
   static constexpr int step = kStep[NN];       // steps per pass of the fast elimination
+  static constexpr int threads = kThreads[NN]; // threads per CTA
 };
 
 // Dynamic shared memory that leaves room for at most `ctas` CTAs of the
@@ -391,7 +392,8 @@ static int condense_dispatch(const polydet_plan_s *pl, const uint32_t *evals, Ev
                              uint32_t *detvals, int ctas_per_sm, cudaStream_t st) {
   if (pl->n == NN) {
     constexpr int T = TeamFor<NN>::value;
-    auto kern = condense_kernel<NN, T, TeamFor<NN>::minb>;
+    constexpr int threads = TeamFor<NN>::threads;
+    auto kern = condense_kernel<NN, T, TeamFor<NN>::minb, threads>;
     const size_t reserve = condense_reserve_bytes(ctas_per_sm);
     if (reserve) {
       static PdPerDevice attr;
@@ -401,7 +403,6 @@ static int condense_dispatch(const polydet_plan_s *pl, const uint32_t *evals, Ev
       });
       if (rc) return rc;
     }
-    const int threads = 128;
     const int64_t teams_per_cta = threads / T;
     EntryOff<NN> off;
     for (int e = 0; e < NN * NN; ++e) off.o[e] = (int64_t)pl->ent[e] * lay.entry;
