@@ -295,6 +295,23 @@ PD_D uint32_t mac2(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, uint32_t 
   return redc((uint64_t)a0 * b0 + (uint64_t)a1 * b1, p, pinv);
 }
 
+// sum_{j<len} x[j] y[j s] / R mod p (x from global memory, y from shared
+// memory with stride s): four products per REDC (redc4: 4 p^2 < p 2^32 for
+// any p < 2^31), then pairs and a single one for the tail.
+PD_D uint32_t dot_strided(const uint32_t *x, const uint32_t *y, int s, int len, uint32_t p, uint32_t pinv) {
+  uint32_t acc = 0u;
+  int j = 0;
+  for (; j + 3 < len; j += 4)
+    acc = addm(acc,
+               redc4((uint64_t)__ldg(x + j) * y[j * s] + (uint64_t)__ldg(x + j + 1) * y[(j + 1) * s] +
+                         (uint64_t)__ldg(x + j + 2) * y[(j + 2) * s] + (uint64_t)__ldg(x + j + 3) * y[(j + 3) * s],
+                     p, pinv),
+               p);
+  for (; j + 1 < len; j += 2) acc = addm(acc, mac2(__ldg(x + j), y[j * s], __ldg(x + j + 1), y[(j + 1) * s], p, pinv), p);
+  if (j < len) acc = addm(acc, mmul(__ldg(x + j), y[j * s], p, pinv), p);
+  return acc;
+}
+
 // X_r = sum_t x_t rho^(t r) for L in {1, 2, 4, 8}; rk[k] = rho^k (Montgomery).
 template <int L>
 PD_D void small_dft(uint32_t (&x)[L], const uint32_t *rk, uint32_t p, uint32_t pinv) {
@@ -371,16 +388,7 @@ __global__ void __launch_bounds__(256) cinterp_kernel(CiArgs a) {
   for (int f = tid; f < L * (Jf + 1) * Ct; f += bd) {
     const int ru = f / Ct, c = f - ru * Ct;
     const int r = ru / (Jf + 1), u = ru - r * (Jf + 1);
-    uint32_t acc = 0u;
-    if (u < Jf) {
-      const uint32_t *row = VfInv + u * Jf;
-      const uint32_t *qv = Qv + (size_t)r * Jf * S + c;
-      int j = 0;
-      for (; j + 1 < Jf; j += 2)
-        acc = addm(acc, mac2(__ldg(row + j), qv[j * S], __ldg(row + j + 1), qv[(j + 1) * S], p, pinv), p);
-      if (j < Jf) acc = addm(acc, mmul(__ldg(row + j), qv[j * S], p, pinv), p);
-    }
-    Qt[ru * S + c] = acc;
+    Qt[ru * S + c] = (u < Jf) ? dot_strided(VfInv + u * Jf, Qv + (size_t)r * Jf * S + c, S, Jf, p, pinv) : 0u;
   }
   __syncthreads();
   if (s > 0) {
@@ -388,14 +396,7 @@ __global__ void __launch_bounds__(256) cinterp_kernel(CiArgs a) {
     for (int f = tid; f < s * L * Ct; f += bd) {
       const int tr = f / Ct, c = f - tr * Ct;
       const int r = tr % L;
-      const uint32_t *h = H + tr * Jf;
-      const uint32_t *qt = Qt + (size_t)r * (Jf + 1) * S + c;
-      uint32_t acc = 0u;
-      int u = 0;
-      for (; u + 1 < Jf; u += 2)
-        acc = addm(acc, mac2(__ldg(h + u), qt[u * S], __ldg(h + u + 1), qt[(u + 1) * S], p, pinv), p);
-      if (u < Jf) acc = addm(acc, mmul(__ldg(h + u), qt[u * S], p, pinv), p);
-      Dv[tr * S + c] = acc;
+      Dv[tr * S + c] = dot_strided(H + tr * Jf, Qt + (size_t)r * (Jf + 1) * S + c, S, Jf, p, pinv);
     }
     __syncthreads();
     // 3b. residuals d_t = y_{Jf L + t} - sum_r partial[t][r] (into row t L)
@@ -442,6 +443,9 @@ static int interp_nodes(polydet_plan_t pl, const uint32_t *detvals, int lo, int 
   const int k = pl->nvars, np = hi - lo;
   const uint64_t slot = pl->interp_ws_words / 2;
   constexpr size_t kMaxSmem = 200 * 1024;
+  int dev = 0, sms = 0;
+  PD_CUDA(cudaGetDevice(&dev));
+  PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   static PdPerDevice attr;
   const int arc = pd_once_per_device(attr, [] {
     PD_CUDA(cudaFuncSetAttribute(cinterp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -468,6 +472,10 @@ static int interp_nodes(polydet_plan_t pl, const uint32_t *detvals, int lo, int 
     int ct = 32;
     while (ct > 1 && rows * (ct + 1) * sizeof(uint32_t) > 48 * 1024) ct >>= 1;
     while (ct > 1 && ct / 2 >= a.A * a.B) ct >>= 1;
+    // small passes (a job's few columns): fewer columns per CTA, so that the
+    // grid still spreads over the SMs (two CTAs each) and every CTA's
+    // phases, which run one after another, are short
+    while (ct > 4 && (a.A * a.B + ct - 1) / ct * np < 2 * sms) ct >>= 1;
     if (rows * (ct + 1) * sizeof(uint32_t) > kMaxSmem) return POLYDET_EINVAL;
     a.Ct = ct;
     a.in = cur;

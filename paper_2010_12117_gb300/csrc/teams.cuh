@@ -10,7 +10,8 @@
 // per order from sweeps on GB300 with random 31-bit matrices and 2^19 nodes:
 // one lane while the whole matrix fits in registers (n <= 12), then 2, 4
 // and 8 lanes; three steps where they beat two by 3 % or more (8-25 % at the
-// orders that take them; at 9, 14, 16, 24 and 32 they tied or lost).
+// orders that take them; at 9, 14, 16, 24 and 32 they tied or lost; at 22
+// two steps on 256-thread CTAs beat three on 128-thread ones).
 // Threads per CTA: the fully unrolled elimination of the large orders is
 // longer than the instruction cache, so fewer, larger CTAs per SM, whose warps
 // walk the same code together, stall less on instruction fetch (ncu at
@@ -24,9 +25,9 @@
 constexpr int kTeam[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2,
                                           2, 2, 2, 4, 4, 4, 4, 4, 8, 8, 8, 8, 8, 8, 8, 8};
 constexpr int kMinBlocks[POLYDET_MAX_N + 1] = {1, 1, 1, 1, 3, 2, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4,
-                                               4, 3, 3, 2, 2, 4, 4, 2, 3, 3, 3, 3, 3, 3, 3, 3};
+                                               4, 3, 3, 2, 2, 2, 4, 2, 3, 3, 3, 3, 3, 3, 3, 3};
 constexpr int kStep[POLYDET_MAX_N + 1] = {2, 2, 2, 2, 2, 2, 2, 2, 3, 2, 3, 3, 3, 3, 2, 3, 2,
-                                          3, 3, 3, 3, 3, 3, 3, 2, 2, 2, 2, 2, 2, 2, 2, 2};
+                                          3, 3, 3, 3, 3, 2, 3, 2, 2, 2, 2, 2, 2, 2, 2, 2};
 constexpr int kThreads[POLYDET_MAX_N + 1] = {128, 128, 128, 128, 128, 128, 128, 128, 128, 128, 128,
                                              128, 128, 128, 128, 128, 128, 128, 128, 128, 256, 256,
-                                             128, 128, 192, 128, 128, 128, 128, 128, 128, 128, 128};
+                                             256, 128, 192, 128, 128, 128, 128, 128, 128, 128, 128};
