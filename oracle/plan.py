@@ -111,7 +111,7 @@ def hadamard_bound_sq(coeffs, degs: Sequence[int]) -> int:
     return min(rows, cols)
 
 
-MIN_PRIMES = 2  # Sec. 4.1: the method always uses at least two big primes
+MIN_PRIMES = 2  # Sec. 4.1: never fewer than two large primes
 
 
 def primes_needed(bound_sq: int, primes: Sequence[int], min_primes: int = MIN_PRIMES) -> int:
