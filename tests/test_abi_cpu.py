@@ -97,6 +97,19 @@ def test_team_sizes_are_usable_and_match_the_tuner():
         binding.team_size(33)
 
 
+def test_condense_steps_cover_every_order():
+    """The fast elimination takes two or three steps per pass at every order
+    (Fast2Step / Fast3Step); orders outside 1..32 are rejected."""
+    ensure_lib()
+    from paper_2010_12117_gb300 import binding
+    steps = [binding.condense_steps(n) for n in range(1, 33)]
+    assert set(steps) <= {2, 3}, steps
+    assert 3 in steps and 2 in steps
+    for bad in (0, 33):
+        with pytest.raises(binding.PolydetError):
+            binding.condense_steps(bad)
+
+
 def _rand_edeg(rng, n, k, dmax, pzero):
     return [[None if rng.random() < pzero else tuple(int(x) for x in rng.integers(0, dmax + 1, k))
              for _ in range(n)] for _ in range(n)]

@@ -270,3 +270,16 @@ def test_invalid_arguments_are_rejected():
         Plan(33, (1,), 2)
     with pytest.raises(PolydetError):
         Plan(4, (3000,), 2)  # N_v beyond 8192
+
+
+def test_integer_pipe_probes_report_ordered_rates():
+    """The probes behind the condensation's roofline: every rate positive and
+    finite, and the element updates ordered by their work (a plain IMAD, then
+    the single-step update of two products, the two-step element of three and
+    the three-step element of four, each under one REDC)."""
+    import math
+    from paper_2010_12117_gb300.binding import probe_int_peaks
+    imad, one, two, three = probe_int_peaks()
+    for r in (imad, one, two, three):
+        assert r > 0 and math.isfinite(r)
+    assert imad > one > two > three
