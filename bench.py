@@ -67,6 +67,11 @@ def _traffic_ratio():
 CRT_PIPE = {"fmaheavy_active": {11: 0.843},
             "sources": {"paper_2010_12117_gb300/csrc/crt.cu": "b7f51ef1688995fc",
                         "paper_2010_12117_gb300/csrc/modarith.cuh": "b36f048e62c9ded4"}}
+# The same for the x_1 pass (coltx_direct_kernel<4, 2>) of the node-grid
+# evaluation (37^3 nodes, 20 primes), the pass that moves its bytes.
+EVAL_PIPE = {"fmaheavy_active": 0.763,
+             "sources": {"paper_2010_12117_gb300/csrc/ntt_direct.cuh": "46390f4078d2117a",
+                         "paper_2010_12117_gb300/csrc/modarith.cuh": "b36f048e62c9ded4"}}
 
 
 WORKLOAD = ("batched: 256 matrices, n~U[4,24], k~U{1,2,3}, d_v~U[1,4], density~U[0.3,1.0], "
@@ -447,6 +452,9 @@ def kernel_leg(st, hbm_peak, mats):
         ws = pl.workspace(P)
         ms = timed(lambda: pl.eval(c, 0, P, ev, ws, st))
         out[f"eval_{name}"] = hbm(ms, 4.0 * P * n2 * (pl.E + pl.G))
+        if not full and _sources_match(EVAL_PIPE["sources"]):
+            # its x_1 pass keeps the integer multiply pipe this busy (ncu)
+            out[f"eval_{name}"]["x1_pass_imad_pipe_active_ncu"] = EVAL_PIPE["fmaheavy_active"]
         dv = torch.empty(P * pl.G, dtype=torch.int32, device="cuda")
         pl.condense(ev, 0, P, dv, st)
         del ev
