@@ -799,7 +799,7 @@ def run_ours(args, world, rank, local):
 
     def model_peak(n_):
         return lanes / slots[step_of[n_]]
-    single_step_upd = lanes / 6.0  # round 1's single-step model, kept for comparison
+    single_step_upd = lanes / 6.0  # the single-step kernel's model (6 slots), kept for comparison
     peak_src = (f"derived: {sms} SMs x 64 IMAD/clk x {sm_mhz:.0f} MHz / IMAD slots per update "
                 "of each order's pass (4.5 for a step pair, 11/3 for a step triple), weighted by "
                 "each order's updates")

@@ -481,7 +481,7 @@ int polydet_mlp_adam(float *params, const float *grads, float *m, float *v, int 
  * updates (a*b + c*d + e*f)/2^32 mod p per second (each stands for two
  * single-step updates) and three-step element updates
  * (a*b + c*d + e*f + g*h)/2^32 mod p per second (each stands for three).
- * Every product takes an operand computed in the previous round, so none is
+ * Every product takes an operand computed in the previous iteration, so none is
  * loop-invariant.  Allocates and frees a small buffer; synchronises
  * `stream`. */
 int polydet_probe_int_peaks(void *stream, double *imad_per_s, double *update_per_s,

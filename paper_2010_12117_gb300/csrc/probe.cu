@@ -3,7 +3,7 @@
 // Four in-register streams with eight independent values per thread, enough
 // warps per SM to hide latency, and no memory traffic.  Every product of an
 // iteration takes at least one operand computed in the previous iteration
-// (value j is updated from values j, j + 1, ... of the last round), so that
+// (value j is updated from values j, j + 1, ... of the last iteration), so that
 // no product is loop-invariant and none can be hoisted out of the loop, as
 // in the elimination, where every operand is a run-time value:
 //  - plain 32-bit multiply-adds (x = x * x + c), the IMAD rate;

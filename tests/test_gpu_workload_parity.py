@@ -2,8 +2,8 @@
 batched form, each checked by the oracle: bit-exact against O2 (integer
 Bareiss after Kronecker packing) where its cost proxy n^3 prod(n d_v + 1) is
 within the CPU budget, otherwise by the Schwartz-Zippel certificate O3 with
-8 independent points mod 2^61 - 1.  The two counts are printed and, when a
-``gpurun_out`` folder exists at the repository root, recorded there as JSON.
+8 independent points mod 2^61 - 1.  The two counts are printed and, when the
+run-output folder exists at the repository root, recorded there as JSON.
 """
 import json
 import multiprocessing
