@@ -145,7 +145,8 @@ static int launch_pass(TxArgs a, int items, int nprimes, cudaStream_t st) {
   // flattened grid below, and not into the interleaved partial layout
   const bool rows_ok = a.B >= 8 || (!a.il_L && ncols * items < ((int64_t)1 << 31) - 256);
   const bool window_ok = a.row_hi == 0 || (a.olp > 1 && a.olp == lp_in && a.row_lo % lp_in == 0);
-  if (!a.inverse && a.Lin <= 8 && rows_ok && window_ok && (a.olp <= 1 || a.olp == lp_in)) {
+  if (!a.inverse && a.Lin <= 8 && a.N <= kDirectTwSmem && rows_ok && window_ok &&
+      (a.olp <= 1 || a.olp == lp_in)) {
     // columns per thread: more share each coset's twiddles, fewer leave
     // fewer idle lanes in the last CTA of a row of B columns (measured: two
     // per thread from rows of about 1000 columns on; four only for inputs of

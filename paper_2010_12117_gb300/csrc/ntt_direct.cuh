@@ -64,13 +64,15 @@ PD_HD int out_rows(const TxArgs &a) { return a.row_hi ? a.row_hi - a.row_lo : a.
 //
 // The integer multiply pipe, which also executes much of the address and
 // move arithmetic, bounds the pass together with the write bandwidth, so the
-// loop is kept lean: the twiddle circle (N <= kDirectTwSmem) is staged in
-// shared memory once per CTA and read with 32-bit indices, and the cosets
-// whose rows are all stored go through one pointer per output row with the
-// columns at fixed offsets from it, without per-store predicates; only the
-// ragged last coset takes the predicated path.
+// loop is kept lean: the twiddle circle is staged in shared memory once per
+// CTA and read with 32-bit indices, and the cosets whose rows are all stored
+// go through one pointer per output row with the columns at fixed offsets
+// from it, without per-store predicates; only the ragged last coset takes
+// the predicated path.  Plans keep D_v <= n d_v, so with at most 8 inputs
+// (d_v <= 7) and n <= 32 a circle has N <= 256 points; launch_pass sends
+// anything longer to the shared-memory pass kernel.
 constexpr int kDirectThreads = 256;
-constexpr int kDirectTwSmem = 2048;
+constexpr int kDirectTwSmem = 256;
 
 // x + y and x - y mod p where ZX / ZY say that x / y is known to be zero.
 template <bool ZX, bool ZY>
@@ -228,12 +230,10 @@ __global__ void __launch_bounds__(kDirectThreads) coltx_direct_kernel(TxArgs a) 
   __shared__ uint32_t s_tw[kDirectTwSmem];
   const int q = a.prime_lo + blockIdx.z;
   const uint32_t *tw = a.tw + (size_t)q * a.tw_len + a.tw_off;
-  // every twiddle index used is below N: j < N / LP and e < LP
-  const bool tw_smem = a.N <= kDirectTwSmem;
-  if (tw_smem) {  // before any thread of the CTA leaves
-    for (int i = threadIdx.x; i < a.N; i += kDirectThreads) s_tw[i] = __ldg(tw + i);
-    __syncthreads();
-  }
+  // every twiddle index used is below N (j < N / LP and e < LP), and
+  // N <= kDirectTwSmem (launch_pass); staged before any thread leaves
+  for (int i = threadIdx.x; i < a.N; i += kDirectThreads) s_tw[i] = __ldg(tw + i);
+  __syncthreads();
   const ModP md = a.mod[q];
   const uint32_t p = md.p, pinv = md.pinv;
   const int64_t ncols = a.A * a.B;
@@ -302,11 +302,6 @@ __global__ void __launch_bounds__(kDirectThreads) coltx_direct_kernel(TxArgs a) 
     for (int k = 0; k < CPT; ++k)
       if (op[k]) op[k] += (jlo - jbeg) * jstep;
   }
-  if (tw_smem) {
-    auto TW = [&](int k) -> uint32_t { return s_tw[k]; };
-    direct_cosets<LIN, CPT>(a, TW, c, op, fast_store, jlo, jhi, ostride, md.r1, p, pinv);
-  } else {
-    auto TW = [&](int k) -> uint32_t { return __ldg(tw + k); };  // the table holds the whole circle
-    direct_cosets<LIN, CPT>(a, TW, c, op, fast_store, jlo, jhi, ostride, md.r1, p, pinv);
-  }
+  auto TW = [&](int k) -> uint32_t { return s_tw[k]; };  // w^k R: the whole circle
+  direct_cosets<LIN, CPT>(a, TW, c, op, fast_store, jlo, jhi, ostride, md.r1, p, pinv);
 }

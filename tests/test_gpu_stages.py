@@ -80,34 +80,6 @@ def test_eval_matches_direct_evaluation(n, degs, P, sample, full):
                 assert int(got[q, e, g]) == modular.eval_point(vec, degs, ex, ws, p), (q, e, g)
 
 
-@pytest.mark.parametrize("n,degs,det_degs", [(2, (3,), (2500,)), (3, (2, 3), (3000, 9))])
-def test_eval_with_a_long_first_variable_grid(n, degs, det_degs):
-    """A declared degree bound far above n d_v (polydet_plan_degrees): the
-    first variable's grid has more than 2048 points, so the register-direct
-    pass reads its twiddles from global memory instead of shared memory."""
-    rng = np.random.default_rng(sum(det_degs))
-    pm = synth.random_matrix(rng, n, degs, 1.0, -(2 ** 31), 2 ** 31)
-    from paper_2010_12117_gb300.binding import Plan as _P
-    P = 2
-    pl = _P(n, degs, P, det_degs=det_degs)
-    assert pl.M[0] == det_degs[0] + 1
-    coeffs = torch.from_numpy(pm.coeffs.astype(np.int32).reshape(-1)).cuda()
-    evals = torch.empty(P * n * n * pl.G, dtype=torch.int32, device="cuda")
-    pl.eval(coeffs, 0, P, evals, pl.workspace(P))
-    torch.cuda.synchronize()
-    got = u32(evals).reshape(P, n * n, pl.G)
-    nodes = sorted(set([0, 1, pl.G - 1] + [int(x) for x in rng.integers(0, pl.G, 40)]))
-    for q in range(P):
-        p = pl.primes[q]
-        for e in range(n * n):
-            vec = pm.coeffs.reshape(n * n, -1)[e].tolist()
-            for g in nodes:
-                idx = modular.grid_index(g, pl.M)
-                ex = [pl.node_exps[v][i] for v, i in enumerate(idx)]
-                assert int(got[q, e, g]) == modular.eval_point(vec, degs, ex, pl.roots[q], p), (q, e, g)
-    pl.close()
-
-
 def test_eval_prime_range_offsets():
     """A range [lo, hi) writes slot 0 for prime lo."""
     n, degs = 4, (2, 2)
