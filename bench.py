@@ -69,8 +69,8 @@ CRT_PIPE = {"fmaheavy_active": {11: 0.843},
                         "paper_2010_12117_gb300/csrc/modarith.cuh": "b36f048e62c9ded4"}}
 # The same for the x_1 pass (coltx_direct_kernel<4, 2>) of the node-grid
 # evaluation (37^3 nodes, 20 primes), the pass that moves its bytes.
-EVAL_PIPE = {"fmaheavy_active": 0.763,
-             "sources": {"paper_2010_12117_gb300/csrc/ntt_direct.cuh": "46390f4078d2117a",
+EVAL_PIPE = {"fmaheavy_active": 0.779,
+             "sources": {"paper_2010_12117_gb300/csrc/ntt_direct.cuh": "cca188a993a99705",
                          "paper_2010_12117_gb300/csrc/modarith.cuh": "b36f048e62c9ded4"}}
 
 
