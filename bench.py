@@ -91,7 +91,7 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
     ap.add_argument("--no-structured", action="store_true")
-    ap.add_argument("--served-jobs", type=int, default=600)
+    ap.add_argument("--served-jobs", type=int, default=2000)
     return ap.parse_args()
 
 

@@ -132,8 +132,11 @@ int polydet_hadamard_primes(int n, const int64_t *entry_l1, int *nprimes_out,
  * block, later plans of that shape copy nothing and allocate only their
  * status word, and the block is kept after the last such plan is destroyed
  * (up to 256 unused shapes, least recently used dropped first;
- * polydet_plan_cache_clear frees them).  No later call allocates device
- * memory: scratch is passed in by the caller.  `flags` is 0 or
+ * polydet_plan_cache_clear frees them).  Blocks and status words come from
+ * the library's own stream-ordered memory pool on its own non-blocking
+ * stream: planning and destroying never synchronise the device.  No later
+ * call allocates device memory: scratch is passed in by the caller.  `flags`
+ * is 0 or
  * POLYDET_FLAG_FULL_GRID.  The plan must be destroyed with
  * polydet_plan_destroy, after the work enqueued with it has completed. */
 int polydet_plan(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg,

@@ -338,8 +338,47 @@ static void interp_tables(uint32_t p32, uint32_t w32, int N, int L, int M, uint3
 // aside, which a batch provides for its jobs).
 // ---------------------------------------------------------------------------
 namespace {
+// Table blocks come from a private stream-ordered memory pool of the device
+// and move on a private non-blocking stream, so that building a new shape or
+// freeing an evicted one (a server's waves plan and drop many shapes) never
+// synchronises the device the way cudaMalloc / cudaFree can: an upload waits
+// for that stream alone, and a free is queued on it.  Tables are freed only
+// once no plan of their shape is left, i.e. after every launch that read them
+// has completed (plans are destroyed after their work, polydet_plan_destroy).
+struct TableArena {
+  cudaStream_t st = nullptr;
+  cudaMemPool_t pool = nullptr;
+};
+std::mutex g_arena_mu;
+TableArena g_arena[64];
+
+int table_arena(TableArena **out) {
+  int dev = 0;
+  PD_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return POLYDET_EINVAL;
+  std::lock_guard<std::mutex> lock(g_arena_mu);
+  TableArena &a = g_arena[dev];
+  if (!a.st) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    PD_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;  // hold freed blocks for the next shapes
+    PD_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    cudaStream_t st = nullptr;
+    PD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    a.pool = pool;
+    a.st = st;
+  }
+  *out = &a;
+  return POLYDET_OK;
+}
+
 struct PlanTables {
   void *dev = nullptr;  // every device table of the shape, packed
+  cudaStream_t st = nullptr;  // its arena's stream (frees are queued there)
   int refs = 0;
   uint64_t last_use = 0;
   bool cached = false;             // held by g_cache (else freed with its last plan)
@@ -369,7 +408,7 @@ void drop_unused(size_t keep) {  // with g_cache_mu held
       if (victim == g_cache.end() || it->second->last_use < victim->second->last_use) victim = it;
     }
     if (unused <= keep || victim == g_cache.end()) return;
-    cudaFree(victim->second->dev);
+    cudaFreeAsync(victim->second->dev, victim->second->st);
     delete victim->second->tmpl;
     delete victim->second;
     g_cache.erase(victim);
@@ -379,12 +418,13 @@ void drop_unused(size_t keep) {  // with g_cache_mu held
 
 static void free_plan(polydet_plan_s *pl) {
   if (!pl) return;
-  if (!pl->status_shared) cudaFree(pl->d_status);
+  if (!pl->status_shared && pl->tables)  // allocated with its tables, on their device's arena
+    cudaFreeAsync(pl->d_status, static_cast<PlanTables *>(pl->tables)->st);
   if (pl->tables) {
     std::lock_guard<std::mutex> lock(g_cache_mu);
     PlanTables *t = static_cast<PlanTables *>(pl->tables);
     if (--t->refs == 0 && !t->cached) {
-      cudaFree(t->dev);
+      cudaFreeAsync(t->dev, t->st);
       delete t->tmpl;
       delete t;
     }
@@ -394,8 +434,17 @@ static void free_plan(polydet_plan_s *pl) {
 }
 
 extern "C" int polydet_plan_cache_clear(void) {
-  std::lock_guard<std::mutex> lock(g_cache_mu);
-  drop_unused(0);
+  {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    drop_unused(0);
+  }
+  // hand the freed blocks back to the device, not only to the pool
+  std::lock_guard<std::mutex> lock(g_arena_mu);
+  for (TableArena &a : g_arena) {
+    if (!a.st) continue;
+    PD_CUDA(cudaStreamSynchronize(a.st));
+    PD_CUDA(cudaMemPoolTrimTo(a.pool, 0));
+  }
   return POLYDET_OK;
 }
 
@@ -419,10 +468,16 @@ static int finish_plan(polydet_plan_s *pl, uint32_t *shared_status, polydet_plan
   } else {
     pl->status_shared = 0;
     pl->d_status = nullptr;
-    cudaError_t e = cudaMalloc((void **)&pl->d_status, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(pl->d_status, 0, sizeof(uint32_t));
+    TableArena *arena = nullptr;
+    const int arc = table_arena(&arena);
+    cudaError_t e = arc ? cudaErrorUnknown
+                        : cudaMallocFromPoolAsync((void **)&pl->d_status, sizeof(uint32_t), arena->pool,
+                                                  arena->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->d_status, 0, sizeof(uint32_t), arena->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(arena->st);
     if (e != cudaSuccess) {
-      pd_set_error("cudaMalloc (status word)", e);
+      pd_set_error("cudaMallocFromPoolAsync (status word)", e);
+      if (pl->d_status && arena) cudaFreeAsync(pl->d_status, arena->st);
       pl->status_shared = 1;  // nothing of its own to free
       free_plan(pl);
       return POLYDET_ENOMEM;
@@ -650,17 +705,26 @@ int pd_plan_impl(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg
   const size_t o_mod = pk.add(mod), o_twf = pk.add(twf), o_twi = pk.add(twi), o_ninv = pk.add(ninv),
                o_rn = pk.add(rn), o_gar = pk.add(garner), o_mh = pk.add(H), o_mf = pk.add(M),
                o_itab = pk.add(itab);
+  TableArena *arena = nullptr;
+  int arc = table_arena(&arena);
+  if (arc) {
+    delete pl;
+    return arc;
+  }
   void *dev = nullptr;
-  cudaError_t e = cudaMalloc(&dev, pk.host.size());
+  cudaError_t e = cudaMallocFromPoolAsync(&dev, pk.host.size(), arena->pool, arena->st);
   if (e != cudaSuccess) {
-    pd_set_error("cudaMalloc", e);
+    pd_set_error("cudaMallocFromPoolAsync", e);
     delete pl;
     return POLYDET_ENOMEM;
   }
-  e = cudaMemcpy(dev, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice);
+  // pageable source: the copy is staged before the call returns; the stream
+  // synchronisation makes the tables visible to every stream that follows
+  e = cudaMemcpyAsync(dev, pk.host.data(), pk.host.size(), cudaMemcpyHostToDevice, arena->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(arena->st);
   if (e != cudaSuccess) {
-    pd_set_error("cudaMemcpy", e);
-    cudaFree(dev);
+    pd_set_error("cudaMemcpyAsync (plan tables)", e);
+    cudaFreeAsync(dev, arena->st);
     delete pl;
     return POLYDET_ECUDA;
   }
@@ -679,6 +743,7 @@ int pd_plan_impl(polydet_plan_t *out, int n, int nvars, const int32_t *entry_deg
   pl->nitems = n * n;
   PlanTables *t = new PlanTables();
   t->dev = dev;
+  t->st = arena->st;
   t->tmpl = new polydet_plan_s(*pl);
   {
     std::lock_guard<std::mutex> lock(g_cache_mu);

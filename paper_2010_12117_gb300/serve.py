@@ -58,12 +58,14 @@ class ServeReport:
     peak_pred_mem: float
     done: List[Done] = field(default_factory=list)
     failed: int = 0  # jobs of waves whose device status word was set
+    host_launch_s: float = 0.0  # host time spent planning and enqueueing waves
 
     def summary(self) -> dict:
         return {"jobs": int(self.jobs), "waves": int(self.waves), "wall_s": float(self.wall_s),
                 "p50_ms": float(self.p50_ms), "p99_ms": float(self.p99_ms), "mean_ms": float(self.mean_ms),
                 "exact_dets_per_s": float(self.exact_dets_per_s), "modp_dets": int(self.modp_dets),
-                "peak_predicted_mem_bytes": float(self.peak_pred_mem), "failed_jobs": int(self.failed)}
+                "peak_predicted_mem_bytes": float(self.peak_pred_mem), "failed_jobs": int(self.failed),
+                "host_launch_s": float(self.host_launch_s)}
 
 
 def measure(pm, stream: torch.cuda.Stream, reps: int = 2) -> tuple:
@@ -129,6 +131,7 @@ class Server:
         waves = 0
         modp = 0
         failed = 0
+        host_launch = 0.0
         t0 = time.perf_counter()
         while nxt < len(order) or pending or inflight:
             now = time.perf_counter() - t0
@@ -198,6 +201,7 @@ class Server:
                     runner.download(st)
                     ev = torch.cuda.Event()
                     ev.record(st)
+                    host_launch += time.perf_counter() - t0 - start
                     modp += runner.modp_dets()
                     inflight.append({"id": waves, "jobs": wave, "runner": runner, "event": ev,
                                      "mem": wm, "slot": slot, "start": start})
@@ -217,4 +221,4 @@ class Server:
         done.sort(key=lambda d: d.idx)
         return ServeReport(len(done), waves, wall, float(np.percentile(lat, 50)),
                            float(np.percentile(lat, 99)), float(lat.mean()),
-                           len(done) / max(wall, 1e-9), modp, peak, done, failed)
+                           len(done) / max(wall, 1e-9), modp, peak, done, failed, host_launch)
