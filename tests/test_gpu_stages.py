@@ -283,3 +283,26 @@ def test_integer_pipe_probes_report_ordered_rates():
     for r in (imad, one, two, three):
         assert r > 0 and math.isfinite(r)
     assert imad > one > two > three
+
+
+def test_shape_cache_eviction_and_clear_keep_results_exact():
+    """More distinct shapes than the cache keeps (256 unused): the oldest
+    shapes' tables go back to the library's pool, a plan of such a shape is
+    built again, and after polydet_plan_cache_clear every table is rebuilt;
+    the determinant of a small job stays the oracle's throughout."""
+    from oracle import bareiss
+    from paper_2010_12117_gb300.binding import Plan as _P, lib
+    from paper_2010_12117_gb300.pipeline import determinant
+    pm = synth.dense_4x4(0)
+    want = bareiss.det_packed(pm.coeffs.tolist(), pm.degs)
+    assert determinant(pm.coeffs, pm.degs).coeffs == want
+    shapes = [(n, (d,), P) for n in range(1, 7) for d in range(1, 6) for P in range(2, 12)]
+    assert len(shapes) > 256
+    for n, degs, P in shapes:
+        _P(n, degs, P).close()
+    assert determinant(pm.coeffs, pm.degs).coeffs == want
+    pl = _P(*shapes[0])  # evicted by now: built again
+    assert pl.P == shapes[0][2]
+    pl.close()
+    assert lib().polydet_plan_cache_clear() == 0
+    assert determinant(pm.coeffs, pm.degs).coeffs == want
