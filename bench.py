@@ -40,7 +40,7 @@ METRIC = ("exact poly determinants/sec and mod-p n×n dets/sec; IMAD % and HBM G
 CONDENSE_TRAFFIC = {"ratio": 1.0133, "fmaheavy_active": 0.716,
                     "sources": {"paper_2010_12117_gb300/csrc/condense.cuh": "b0dcc202ebcb755b",
                                 "paper_2010_12117_gb300/csrc/modarith.cuh": "b36f048e62c9ded4",
-                                "paper_2010_12117_gb300/csrc/teams.cuh": "c8e304d8cce1aaeb"}}
+                                "paper_2010_12117_gb300/csrc/teams.cuh": "2b54f7c70ebf5672"}}
 
 
 def _code_digest(path: str) -> str:
